@@ -1,0 +1,186 @@
+/*
+ * rr.h -- C ABI of the GB300 randomized-resolvent library (librr.so).
+ *
+ * Randomized resolvent analysis (Ribeiro, Yeh & Taira, arXiv:1902.01458):
+ * for a discretised linearised flow operator L (Sec. II.A, Eq. 1) and a
+ * complex shift s = i*omega (+ beta for the discounted resolvent, Sec. II.A),
+ * the weighted resolvent is
+ *
+ *     R = W^{1/2} (s I - L)^{-1} W^{-1/2}                    (Eq. 4)
+ *
+ * and Algorithm 1 (Sec. II.B) approximates its leading singular triplets
+ * (Eq. 5) from k solves with a Gaussian test matrix, k adjoint solves and k
+ * recovery solves (Eq. 8), all reusing one factorisation per shift
+ * (Sec. III.A).  W is diagonal and positive (identity when not given).
+ *
+ * Conventions for every entry point
+ *  - Every call returns rr_status and never aborts; rr_last_error() gives a
+ *    one-line message for the calling thread's most recent failure.
+ *  - Complex numbers are interleaved (re, im) pairs of doubles (complex128).
+ *  - Unknowns are ordered by streamwise column, n = ((ix*ny)+iy)*q + c, so
+ *    the operator is block-tridiagonal with b x b blocks, b = q*ny.
+ *  - Batches: a factors object holds F shifts ("problems").  Block vectors
+ *    are device arrays laid out [F][N][k] (row-major; column j of problem f
+ *    is the strided vector x[f*N*k + n*k + j]).
+ *  - Device pointers must be on the operator's device; host pointers are
+ *    read before the call returns.  The caller owns every pointer it
+ *    passes; the library owns the opaque handles, which are created and
+ *    destroyed in pairs.
+ *  - Work is issued on the stream given to rr_factor (or rr_apply/rr_phi).
+ *    Calls that iterate (refinement) or report rr_info synchronise that
+ *    stream before returning; the others return once the work is queued.
+ */
+#ifndef RR_H
+#define RR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RR_OK = 0,
+  RR_ERR_ARG = 1,         /* invalid argument (null, size, kind, range)      */
+  RR_ERR_NOMEM = 2,       /* device allocation failed                        */
+  RR_ERR_SINGULAR = 3,    /* zero pivot in the block factorisation           */
+  RR_ERR_NOCONV = 4,      /* refinement hit max_refine above refine_tol      */
+  RR_ERR_RANK = 5,        /* CholeskyQR breakdown even with the shift        */
+  RR_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up              */
+  RR_ERR_CUDA = 7,        /* CUDA runtime error (message in rr_last_error)   */
+  RR_ERR_UNSUPPORTED = 8  /* valid request this build does not implement     */
+} rr_status;
+
+/* Arithmetic of the block factorisation and the block sweeps.  FP64 runs
+ * everything in complex double.  FP32 stores the factors and runs the
+ * sweeps in complex float and wins accuracy back by iterative refinement
+ * against an FP64 residual; QR, SVD, norms and the refinement residual stay
+ * FP64 in every mode. */
+typedef enum { RR_FP64 = 0, RR_FP32 = 1 } rr_precision;
+
+/* Operator kinds (q = unknowns per grid point). */
+enum { RR_ADVDIFF_SCALAR = 1, RR_ISO_NS2D = 3 };
+
+/* Uniform grid of nx x ny interior nodes on [x0,x1] x [y0,y1].
+ * Dirichlet directions have spacing L/(n+1) and zero ghost nodes; a periodic
+ * y direction (periodic_y != 0) has spacing (y1-y0)/ny and nodes y0+j*dy.
+ *  RR_ADVDIFF_SCALAR: L phi = -U phi_x - V phi_y + (1/re) lap phi - s_s phi
+ *  RR_ISO_NS2D: isothermal compressible Navier-Stokes in (rho', u', v')
+ *    linearised about (rho, U, V), p = rho / mach^2, Reynolds number re,
+ *    second-order central differences (4-corner cross derivative).
+ * Sponge s_s = sponge_max * xi^2 on the outer sponge_frac of each
+ * (non-periodic) boundary, xi the normalised depth into the layer. */
+typedef struct {
+  int kind;
+  int nx, ny;
+  int periodic_y;
+  double x0, x1, y0, y1;
+  double re;
+  double mach;
+  double sponge_max;
+  double sponge_frac;
+} rr_grid;
+
+/* Base-flow fields on the interior nodes, host pointers to nx*ny doubles
+ * each, point index ix*ny + iy.  rho may be NULL for RR_ADVDIFF_SCALAR. */
+typedef struct {
+  const double* rho;
+  const double* u;
+  const double* v;
+} rr_baseflow;
+
+typedef struct rr_operator rr_operator; /* device copy of L's stencil      */
+typedef struct rr_factors rr_factors;   /* block factors of F shifts       */
+
+/* Diagnostics of one rr_solve / rr_sketch / rr_modes call. */
+typedef struct {
+  int refine_iters;       /* largest refinement count over all solves      */
+  double refine_residual; /* largest final ||b - A x|| / ||b|| per column  */
+  double cqr_cond;        /* largest condition estimate of a CholeskyQR R  */
+  int cqr_shifted;        /* 1 if a shifted CholeskyQR fallback was used   */
+} rr_info;
+
+const char* rr_last_error(void);
+const char* rr_status_string(rr_status s);
+
+/* Build the stencil of L (Sec. II.A, Eq. 1; the discrete operator of the
+ * grid kind above) on `device` from host base-flow fields.  weights: NULL
+ * (identity) or N = nx*ny*q positive doubles (host), the diagonal of W.
+ * Errors: RR_ERR_ARG (kind, nx or ny < 3, b = q*ny > 1024, non-positive
+ * weight, re <= 0, mach <= 0 for NS), RR_ERR_NOMEM, RR_ERR_CUDA. */
+rr_status rr_create_operator(const rr_grid* grid, const rr_baseflow* flow,
+                             const double* weights, int device,
+                             rr_operator** out);
+rr_status rr_destroy_operator(rr_operator* op);
+
+/* Sizes of an operator: N unknowns, block size b, q, nx, ny. */
+rr_status rr_operator_dims(const rr_operator* op, int* n, int* b, int* q,
+                           int* nx, int* ny);
+
+/* y = (s_f I - L) x for F shifts (adjoint != 0: y = (s_f I - L)^H x).
+ * shifts: host, 2*F doubles (re, im).  x, y: device complex128 [F][N][k],
+ * distinct buffers.  This is the FP64 residual operator of the refinement
+ * (Sec. II.A's operator applied, no solve). */
+rr_status rr_apply(rr_operator* op, int nshift, const double* shifts, int k,
+                   int adjoint, const void* x, void* y, void* stream);
+
+/* Eq. (9): Phi_j = ||grad v||_F at every grid point, repeated over the q
+ * variables.  phi: device, N doubles. */
+rr_status rr_phi(rr_operator* op, double* phi, void* stream);
+
+/* Factor s_f I - L for F shifts (Sec. III.A: one factorisation per shift,
+ * reused by all solves).  shifts: host, 2*F doubles.  Block LU over the
+ * streamwise columns with an explicit inverse of every Schur block by
+ * Gauss-Jordan elimination with partial pivoting.  stream: a cudaStream_t
+ * (NULL = default stream) used by every later call on the factors.
+ * Errors: RR_ERR_ARG, RR_ERR_NOMEM, RR_ERR_SINGULAR (exact zero pivot in some
+ * Schur block; the factors are still returned), RR_ERR_CUDA. */
+rr_status rr_factor(rr_operator* op, int nshift, const double* shifts,
+                    rr_precision prec, void* stream, rr_factors** out);
+rr_status rr_destroy_factors(rr_factors* f);
+
+/* x = R b (adjoint = 0) or x = R^H b (adjoint != 0) for every problem: the
+ * solve of Algorithm 1's second, fourth and sixth steps.  b, x: device
+ * complex128 [F][N][k], distinct.  refine_tol / max_refine drive the FP64
+ * iterative refinement (FP32 factors only; ignored for FP64).  info may be
+ * NULL.  Errors: RR_ERR_ARG, RR_ERR_NOCONV (x still written), RR_ERR_CUDA. */
+rr_status rr_solve(rr_factors* f, int k, int adjoint, const void* b, void* x,
+                   double refine_tol, int max_refine, rr_info* info);
+
+/* Algorithm 1, first five steps, for every problem: Omega = randn(N, k)
+ * (Philox-4x32-10 with key seeds[f], counter (n, j, 0, 0), Box-Muller),
+ * optionally Omega_p = diag(phi) Omega (Eq. 9; phi: device, N doubles, or
+ * NULL); Y = R Omega; Q = qr(Y) (FP64 CholeskyQR2); B^H = R^H Q; the SVD of
+ * B from CholeskyQR2 of B^H and a k x k one-sided Jacobi SVD.
+ * seeds: host, F values.  Outputs (device): V [F][N][k] forcing modes and
+ * sigma_halko [F][k] (singular values of B, descending).  1 <= k <= 64,
+ * k <= N.  Errors: RR_ERR_ARG, RR_ERR_NOCONV, RR_ERR_RANK, RR_ERR_CUDA. */
+rr_status rr_sketch(rr_factors* f, int k, const uint64_t* seeds,
+                    const double* phi, double refine_tol, int max_refine,
+                    void* V, double* sigma_halko, rr_info* info);
+
+/* Algorithm 1, last steps (Eq. 8): U Sigma = R V, sigma_j = ||(U Sigma)_j||,
+ * u_j = (U Sigma)_j / sigma_j; with orthogonalize != 0 also the optional
+ * SVD(U Sigma) = U Sigma Vt^H and V <- V Vt.  Results are sorted by sigma
+ * descending and each v_j is phase-normalised (largest-modulus entry, lowest
+ * index on ties, real positive; u_j takes the same phase).  V is in/out
+ * [F][N][k]; U [F][N][k]; sigma [F][k]; all device.  Errors as rr_sketch. */
+rr_status rr_modes(rr_factors* f, int k, void* V, void* U, double* sigma,
+                   int orthogonalize, double refine_tol, int max_refine,
+                   rr_info* info);
+
+/* Algorithm 1, first step: the test matrix alone.  omega[f][n][j] =
+ * phi[n] * g(seeds[f], n, j) (phi NULL: 1), g the Philox-4x32-10 + Box-Muller
+ * normal deviate described at rr_sketch; imaginary parts are zero.  seeds:
+ * host, nshift values; phi, omega: device (omega complex128 [F][N][k]). */
+rr_status rr_gaussian(int nshift, int n, int k, const uint64_t* seeds, const double* phi,
+                      void* omega, void* stream);
+
+/* Number of problems (shifts) and precision of a factors object. */
+rr_status rr_factors_dims(const rr_factors* f, int* nshift, int* prec);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RR_H */

@@ -1,0 +1,328 @@
+"""ctypes binding of librr's C ABI (include/rr.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts Python
+and torch arguments to pointers and sizes, and raises RRError on a non-zero
+status.  Device buffers are torch tensors (complex128 / float64, contiguous,
+on the operator's device); block vectors have shape [F, N, k].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librr.so")
+
+RR_OK = 0
+STATUS = {0: "RR_OK", 1: "RR_ERR_ARG", 2: "RR_ERR_NOMEM", 3: "RR_ERR_SINGULAR",
+          4: "RR_ERR_NOCONV", 5: "RR_ERR_RANK", 6: "RR_ERR_TIMEOUT",
+          7: "RR_ERR_CUDA", 8: "RR_ERR_UNSUPPORTED"}
+PRECISION = {"fp64": 0, "fp32": 1}
+ADVDIFF, NS2D = 1, 3
+
+
+class RRError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class rr_grid(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("periodic_y", ctypes.c_int), ("x0", ctypes.c_double),
+                ("x1", ctypes.c_double), ("y0", ctypes.c_double),
+                ("y1", ctypes.c_double), ("re", ctypes.c_double),
+                ("mach", ctypes.c_double), ("sponge_max", ctypes.c_double),
+                ("sponge_frac", ctypes.c_double)]
+
+
+class rr_baseflow(ctypes.Structure):
+    _fields_ = [("rho", ctypes.POINTER(ctypes.c_double)),
+                ("u", ctypes.POINTER(ctypes.c_double)),
+                ("v", ctypes.POINTER(ctypes.c_double))]
+
+
+class rr_info(ctypes.Structure):
+    _fields_ = [("refine_iters", ctypes.c_int), ("refine_residual", ctypes.c_double),
+                ("cqr_cond", ctypes.c_double), ("cqr_shifted", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# exported symbol -> (restype, argtypes)
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+SIGNATURES = {
+    "rr_last_error": (ctypes.c_char_p, []),
+    "rr_status_string": (ctypes.c_char_p, [_I]),
+    "rr_create_operator": (_I, [ctypes.POINTER(rr_grid), ctypes.POINTER(rr_baseflow),
+                                ctypes.POINTER(ctypes.c_double), _I,
+                                ctypes.POINTER(_P)]),
+    "rr_destroy_operator": (_I, [_P]),
+    "rr_operator_dims": (_I, [_P] + [ctypes.POINTER(_I)] * 5),
+    "rr_apply": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), _I, _I, _P, _P, _P]),
+    "rr_phi": (_I, [_P, _P, _P]),
+    "rr_factor": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), _I, _P,
+                       ctypes.POINTER(_P)]),
+    "rr_destroy_factors": (_I, [_P]),
+    "rr_factors_dims": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "rr_solve": (_I, [_P, _I, _I, _P, _P, _D, _I, ctypes.POINTER(rr_info)]),
+    "rr_sketch": (_I, [_P, _I, ctypes.POINTER(ctypes.c_uint64), _P, _D, _I, _P, _P,
+                       ctypes.POINTER(rr_info)]),
+    "rr_modes": (_I, [_P, _I, _P, _P, _P, _I, _D, _I, ctypes.POINTER(rr_info)]),
+    "rr_gaussian": (_I, [_I, _I, _I, ctypes.POINTER(ctypes.c_uint64), _P, _P, _P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load librr.so (built by build.build()); no fallback if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"librr.so not found at {path}: build it with "
+            "paper_1902_01458_gb300.build.build() (there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != RR_OK:
+        msg = load().rr_last_error().decode(errors="replace")
+        raise RRError(status, msg)
+
+
+def _dptr(t) -> int:
+    """Device pointer of a contiguous torch tensor."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _shift_array(shifts) -> ctypes.Array:
+    s = np.asarray(shifts, dtype=np.complex128).ravel()
+    flat = np.empty(2 * s.size, dtype=np.float64)
+    flat[0::2] = s.real
+    flat[1::2] = s.imag
+    return (ctypes.c_double * flat.size)(*flat.tolist())
+
+
+# ------------------------------------------------------------ the C calls
+def rr_create_operator(grid, rho, u, v, weights=None, device: int = 0):
+    lib = load()
+    g = rr_grid(int(grid.kind), int(grid.nx), int(grid.ny), int(bool(grid.periodic_y)),
+                float(grid.x0), float(grid.x1), float(grid.y0), float(grid.y1),
+                float(grid.re), float(getattr(grid, "mach", 0.0)),
+                float(getattr(grid, "sponge_max", 0.0)),
+                float(getattr(grid, "sponge_frac", 0.1)))
+    keep = []
+
+    def arr(a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel())
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    fl = rr_baseflow(arr(rho), arr(u), arr(v))
+    w = arr(weights)
+    h = ctypes.c_void_p()
+    _check(lib.rr_create_operator(ctypes.byref(g), ctypes.byref(fl), w, int(device),
+                                  ctypes.byref(h)))
+    return h
+
+
+def rr_destroy_operator(h):
+    if h:
+        _check(load().rr_destroy_operator(h))
+
+
+def rr_operator_dims(h):
+    vals = [ctypes.c_int() for _ in range(5)]
+    _check(load().rr_operator_dims(h, *[ctypes.byref(v) for v in vals]))
+    return tuple(v.value for v in vals)
+
+
+def rr_apply(h, shifts, x, y, adjoint=False, stream=None):
+    F, _, k = x.shape
+    _check(load().rr_apply(h, F, _shift_array(shifts), k, int(adjoint), _dptr(x),
+                           _dptr(y), _stream_ptr(stream)))
+
+
+def rr_phi(h, phi, stream=None):
+    _check(load().rr_phi(h, _dptr(phi), _stream_ptr(stream)))
+
+
+def rr_factor(h, shifts, precision="fp64", stream=None):
+    s = np.asarray(shifts, dtype=np.complex128).ravel()
+    out = ctypes.c_void_p()
+    st = load().rr_factor(h, s.size, _shift_array(s), PRECISION[precision],
+                          _stream_ptr(stream), ctypes.byref(out))
+    if st != RR_OK and out:
+        load().rr_destroy_factors(out)
+    _check(st)
+    return out
+
+
+def rr_destroy_factors(h):
+    if h:
+        _check(load().rr_destroy_factors(h))
+
+
+def rr_solve(h, b, x, adjoint=False, refine_tol=1e-10, max_refine=10):
+    info = rr_info()
+    _, _, k = b.shape
+    st = load().rr_solve(h, k, int(adjoint), _dptr(b), _dptr(x), float(refine_tol),
+                         int(max_refine), ctypes.byref(info))
+    return st, info
+
+
+def rr_sketch(h, k, seeds, phi, V, sigma_halko, refine_tol=1e-10, max_refine=10):
+    info = rr_info()
+    sd = np.asarray(seeds, dtype=np.uint64).ravel()
+    arr = (ctypes.c_uint64 * sd.size)(*[int(x) for x in sd])
+    st = load().rr_sketch(h, int(k), arr, None if phi is None else _dptr(phi),
+                          float(refine_tol), int(max_refine), _dptr(V),
+                          _dptr(sigma_halko), ctypes.byref(info))
+    return st, info
+
+
+def rr_modes(h, k, V, U, sigma, orthogonalize=False, refine_tol=1e-10, max_refine=10):
+    info = rr_info()
+    st = load().rr_modes(h, int(k), _dptr(V), _dptr(U), _dptr(sigma), int(orthogonalize),
+                         float(refine_tol), int(max_refine), ctypes.byref(info))
+    return st, info
+
+
+def rr_gaussian(seeds, n, k, phi, omega, stream=None):
+    sd = np.asarray(seeds, dtype=np.uint64).ravel()
+    arr = (ctypes.c_uint64 * sd.size)(*[int(x) for x in sd])
+    _check(load().rr_gaussian(sd.size, int(n), int(k), arr,
+                              None if phi is None else _dptr(phi), _dptr(omega),
+                              _stream_ptr(stream)))
+
+
+# ---------------------------------------------------------- thin wrappers
+@dataclass
+class ResolventResult:
+    sigma: "object"          # [F, k] float64 (device)
+    sigma_halko: "object"    # [F, k]
+    U: "object"              # [F, N, k] complex128
+    V: "object"              # [F, N, k]
+    info: dict
+
+
+class Operator:
+    """Owns an rr_operator handle (device copy of the stencil of L)."""
+
+    def __init__(self, grid, flow, weights=None, device: int = 0):
+        rho = getattr(flow, "rho", None)
+        self.device = device
+        self.handle = rr_create_operator(grid, rho, flow.u, flow.v, weights, device)
+        self.n, self.b, self.q, self.nx, self.ny = rr_operator_dims(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rr_destroy_operator(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, shifts, x, adjoint=False):
+        import torch
+        y = torch.empty_like(x)
+        rr_apply(self.handle, shifts, x, y, adjoint)
+        return y
+
+    def phi(self):
+        import torch
+        p = torch.empty(self.n, dtype=torch.float64, device=f"cuda:{self.device}")
+        rr_phi(self.handle, p)
+        torch.cuda.synchronize(self.device)
+        return p
+
+    def factor(self, shifts, precision="fp64", stream=None) -> "Factors":
+        return Factors(self, shifts, precision, stream)
+
+
+class Factors:
+    """Owns an rr_factors handle: the block factors of F shifts."""
+
+    def __init__(self, op: Operator, shifts, precision="fp64", stream=None):
+        self.op = op
+        self.shifts = np.asarray(shifts, dtype=np.complex128).ravel()
+        self.F = self.shifts.size
+        self.precision = precision
+        self.handle = rr_factor(op.handle, self.shifts, precision, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rr_destroy_factors(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self):
+        return f"cuda:{self.op.device}"
+
+    def solve(self, b, adjoint=False, refine_tol=1e-10, max_refine=10, check=True):
+        import torch
+        x = torch.empty_like(b)
+        st, info = rr_solve(self.handle, b, x, adjoint, refine_tol, max_refine)
+        if check:
+            _check(st)
+        return x, info.as_dict()
+
+    def sketch(self, k, seeds, phi=None, refine_tol=1e-10, max_refine=10):
+        import torch
+        V = torch.empty(self.F, self.op.n, k, dtype=torch.complex128, device=self._dev())
+        sh = torch.empty(self.F, k, dtype=torch.float64, device=self._dev())
+        st, info = rr_sketch(self.handle, k, seeds, phi, V, sh, refine_tol, max_refine)
+        _check(st)
+        return V, sh, info.as_dict()
+
+    def modes(self, V, orthogonalize=False, refine_tol=1e-10, max_refine=10):
+        import torch
+        k = V.shape[2]
+        U = torch.empty_like(V)
+        sig = torch.empty(self.F, k, dtype=torch.float64, device=self._dev())
+        st, info = rr_modes(self.handle, k, V, U, sig, orthogonalize, refine_tol,
+                            max_refine)
+        _check(st)
+        return U, sig, info.as_dict()
+
+    def randomized_resolvent(self, k, seeds, phi=None, orthogonalize=False,
+                             refine_tol=1e-10, max_refine=10) -> ResolventResult:
+        """Algorithm 1 for every shift of the batch."""
+        V, sh, i1 = self.sketch(k, seeds, phi, refine_tol, max_refine)
+        U, sig, i2 = self.modes(V, orthogonalize, refine_tol, max_refine)
+        info = {key: max(i1[key], i2[key]) for key in i1}
+        return ResolventResult(sig, sh, U, V, info)

@@ -1,0 +1,288 @@
+// Operator assembly (Sec. II.A, Eq. 1), the FP64 operator application used
+// by the refinement residual, and the sketch weight Phi of Eq. (9).
+//
+// Each grid point evaluates its own stencil: base-flow derivatives from its
+// neighbours (central differences, first-order one-sided at the first/last
+// node, second derivatives re-centred on the inner neighbour there), then the
+// 9 x q x q coefficients of the linearised equations.
+#include "rr_internal.cuh"
+
+namespace {
+
+struct Field {
+  const double* f;
+  int nx, ny, periodic;
+  double dx, dy;
+  __device__ double at(int i, int j) const { return f[i * ny + j]; }
+  __device__ int wrap(int j) const { return (j + ny) % ny; }
+  __device__ double d1x(int i, int j) const {
+    if (i == 0) return (at(1, j) - at(0, j)) / dx;
+    if (i == nx - 1) return (at(nx - 1, j) - at(nx - 2, j)) / dx;
+    return (at(i + 1, j) - at(i - 1, j)) / (2.0 * dx);
+  }
+  __device__ double d1y(int i, int j) const {
+    if (periodic) return (at(i, wrap(j + 1)) - at(i, wrap(j - 1))) / (2.0 * dy);
+    if (j == 0) return (at(i, 1) - at(i, 0)) / dy;
+    if (j == ny - 1) return (at(i, ny - 1) - at(i, ny - 2)) / dy;
+    return (at(i, j + 1) - at(i, j - 1)) / (2.0 * dy);
+  }
+  __device__ double d2x(int i, int j) const {
+    int c = min(max(i, 1), nx - 2);
+    return (at(c - 1, j) - 2.0 * at(c, j) + at(c + 1, j)) / (dx * dx);
+  }
+  __device__ double d2y(int i, int j) const {
+    if (periodic)
+      return (at(i, wrap(j - 1)) - 2.0 * at(i, j) + at(i, wrap(j + 1))) / (dy * dy);
+    int c = min(max(j, 1), ny - 2);
+    return (at(i, c - 1) - 2.0 * at(i, c) + at(i, c + 1)) / (dy * dy);
+  }
+  // d/dx of the y-derivative field
+  __device__ double dxy(int i, int j) const {
+    if (i == 0) return (d1y(1, j) - d1y(0, j)) / dx;
+    if (i == nx - 1) return (d1y(nx - 1, j) - d1y(nx - 2, j)) / dx;
+    return (d1y(i + 1, j) - d1y(i - 1, j)) / (2.0 * dx);
+  }
+};
+
+struct AsmParams {
+  int kind, q, nx, ny, periodic;
+  double dx, dy, x0, x1, y0, y1, re, c2, smax, sfrac;
+};
+
+__device__ double sponge_at(const AsmParams& p, int i, int j) {
+  if (p.smax == 0.0) return 0.0;
+  double x = p.x0 + (i + 1) * p.dx;
+  double lx = p.sfrac * (p.x1 - p.x0);
+  double xi = fmax(fmax((p.x0 + lx - x) / lx, (x - (p.x1 - lx)) / lx), 0.0);
+  xi = fmin(xi, 1.0);
+  double s = p.smax * xi * xi;
+  if (!p.periodic) {
+    double y = p.y0 + (j + 1) * p.dy;
+    double ly = p.sfrac * (p.y1 - p.y0);
+    double eta = fmax(fmax((p.y0 + ly - y) / ly, (y - (p.y1 - ly)) / ly), 0.0);
+    eta = fmin(eta, 1.0);
+    s = fmax(s, p.smax * eta * eta);
+  }
+  return s;
+}
+
+// slot index of stencil offset (dx, dy)
+__device__ __forceinline__ int slot(int dx, int dy) { return (dx + 1) * 3 + (dy + 1); }
+
+__global__ void assemble_kernel(AsmParams p, const double* __restrict__ flow,
+                                double* __restrict__ coef) {
+  int pt = blockIdx.x * blockDim.x + threadIdx.x;
+  int npts = p.nx * p.ny;
+  if (pt >= npts) return;
+  int i = pt / p.ny, j = pt % p.ny;
+  const int q = p.q, S = 9 * q;
+  double c[3][9][3];
+  for (int a = 0; a < 3; ++a)
+    for (int s = 0; s < 9; ++s)
+      for (int b = 0; b < 3; ++b) c[a][s][b] = 0.0;
+
+  Field R{flow, p.nx, p.ny, p.periodic, p.dx, p.dy};
+  Field U{flow + npts, p.nx, p.ny, p.periodic, p.dx, p.dy};
+  Field V{flow + 2 * npts, p.nx, p.ny, p.periodic, p.dx, p.dy};
+  const double u = U.at(i, j), v = V.at(i, j);
+  const double hx = 1.0 / (2.0 * p.dx), hy = 1.0 / (2.0 * p.dy);
+  const double ixx = 1.0 / (p.dx * p.dx), iyy = 1.0 / (p.dy * p.dy);
+  const double ixy = 1.0 / (4.0 * p.dx * p.dy);
+  const double sg = sponge_at(p, i, j);
+
+  // generic pieces: coefficient a * (difference operator) added to c[o][.][in]
+  auto addDx = [&](int o, int in, double a) {
+    c[o][slot(1, 0)][in] += a * hx;
+    c[o][slot(-1, 0)][in] -= a * hx;
+  };
+  auto addDy = [&](int o, int in, double a) {
+    c[o][slot(0, 1)][in] += a * hy;
+    c[o][slot(0, -1)][in] -= a * hy;
+  };
+  auto addDxx = [&](int o, int in, double a) {
+    c[o][slot(1, 0)][in] += a * ixx;
+    c[o][slot(-1, 0)][in] += a * ixx;
+    c[o][slot(0, 0)][in] -= 2.0 * a * ixx;
+  };
+  auto addDyy = [&](int o, int in, double a) {
+    c[o][slot(0, 1)][in] += a * iyy;
+    c[o][slot(0, -1)][in] += a * iyy;
+    c[o][slot(0, 0)][in] -= 2.0 * a * iyy;
+  };
+  auto addDxy = [&](int o, int in, double a) {
+    c[o][slot(1, 1)][in] += a * ixy;
+    c[o][slot(-1, -1)][in] += a * ixy;
+    c[o][slot(1, -1)][in] -= a * ixy;
+    c[o][slot(-1, 1)][in] -= a * ixy;
+  };
+  auto addDiag = [&](int o, int in, double a) { c[o][slot(0, 0)][in] += a; };
+
+  if (p.kind == RR_ADVDIFF_SCALAR) {
+    const double nu = 1.0 / p.re;
+    addDx(0, 0, -u);
+    addDy(0, 0, -v);
+    addDxx(0, 0, nu);
+    addDyy(0, 0, nu);
+    addDiag(0, 0, -sg);
+  } else {
+    const double rho = R.at(i, j);
+    const double Ux = U.d1x(i, j), Uy = U.d1y(i, j);
+    const double Vx = V.d1x(i, j), Vy = V.d1y(i, j);
+    const double Rx = R.d1x(i, j), Ry = R.d1y(i, j);
+    const double Uxx = U.d2x(i, j), Uyy = U.d2y(i, j), Uxy = U.dxy(i, j);
+    const double Vxx = V.d2x(i, j), Vyy = V.d2y(i, j), Vxy = V.dxy(i, j);
+    const double c2 = p.c2, re = p.re;
+    const double mu = 1.0 / (rho * re);
+    // viscous force of the base flow per unit mass (multiplies -rho'/rho^2 * rho)
+    const double fu = (Uxx + Uyy + (Uxx + Vxy) / 3.0) / re;
+    const double fv = (Vxx + Vyy + (Uxy + Vyy) / 3.0) / re;
+    // continuity
+    addDx(0, 0, -u); addDy(0, 0, -v); addDiag(0, 0, -(Ux + Vy) - sg);
+    addDx(0, 1, -rho); addDiag(0, 1, -Rx);
+    addDy(0, 2, -rho); addDiag(0, 2, -Ry);
+    // x-momentum
+    addDx(1, 0, -c2 / rho); addDiag(1, 0, c2 * Rx / (rho * rho) - fu / (rho * rho));
+    addDx(1, 1, -u); addDy(1, 1, -v);
+    addDxx(1, 1, mu * (4.0 / 3.0)); addDyy(1, 1, mu);
+    addDiag(1, 1, -Ux - sg);
+    addDxy(1, 2, mu / 3.0); addDiag(1, 2, -Uy);
+    // y-momentum
+    addDy(2, 0, -c2 / rho); addDiag(2, 0, c2 * Ry / (rho * rho) - fv / (rho * rho));
+    addDxy(2, 1, mu / 3.0); addDiag(2, 1, -Vx);
+    addDx(2, 2, -u); addDy(2, 2, -v);
+    addDxx(2, 2, mu); addDyy(2, 2, mu * (4.0 / 3.0));
+    addDiag(2, 2, -Vy - sg);
+  }
+
+  for (int dxo = -1; dxo <= 1; ++dxo)
+    for (int dyo = -1; dyo <= 1; ++dyo) {
+      bool ok = (i + dxo >= 0 && i + dxo < p.nx) &&
+                (p.periodic || (j + dyo >= 0 && j + dyo < p.ny));
+      if (!ok)
+        for (int a = 0; a < q; ++a)
+          for (int b = 0; b < q; ++b) c[a][slot(dxo, dyo)][b] = 0.0;
+    }
+  for (int a = 0; a < q; ++a) {
+    double* out = coef + (size_t)(pt * q + a) * S;
+    for (int s = 0; s < 9; ++s)
+      for (int b = 0; b < q; ++b) out[s * q + b] = c[a][s][b];
+  }
+}
+
+// y = (s I - L) x (adjoint: (s I - L)^H x), optionally r = b - that.
+template <bool RESID>
+__global__ void apply_kernel(OpView op, const double2* __restrict__ shifts, int F, int k,
+                             int adjoint, const double2* __restrict__ bvec,
+                             const double2* __restrict__ x, double2* __restrict__ y) {
+  const size_t total = (size_t)F * op.n * k;
+  const size_t NK = (size_t)op.n * k;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int f = (int)(e / NK);
+    size_t rem = e - (size_t)f * NK;
+    int n = (int)(rem / k);
+    int j = (int)(rem - (size_t)n * k);
+    const double2* xf = x + (size_t)f * NK;
+    double2 s = shifts[f];
+    if (adjoint) s.y = -s.y;
+    double2 acc = cmul(s, xf[(size_t)n * k + j]);
+    int c = n % op.q;
+    int pt = n / op.q;
+    int ix = pt / op.ny, iy = pt % op.ny;
+    if (!adjoint) {
+      const double* cf = op.coef + (size_t)n * op.S;
+      for (int dx = -1; dx <= 1; ++dx) {
+        int jx = ix + dx;
+        if (jx < 0 || jx >= op.nx) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+          int jy = nbr_y(iy, dy, op.ny, op.periodic);
+          if (jy < 0) continue;
+          int base = ((jx * op.ny + jy) * op.q);
+          const double* cs = cf + ((dx + 1) * 3 + (dy + 1)) * op.q;
+          for (int cp = 0; cp < op.q; ++cp)
+            acc = crfma(-cs[cp], xf[(size_t)(base + cp) * k + j], acc);
+        }
+      }
+    } else {
+      // (L^T x)[m] = sum over rows r whose stencil reaches m
+      for (int dx = -1; dx <= 1; ++dx) {
+        int rx = ix - dx;
+        if (rx < 0 || rx >= op.nx) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+          int ry = nbr_y(iy, -dy, op.ny, op.periodic);
+          if (ry < 0) continue;
+          int base = (rx * op.ny + ry) * op.q;
+          for (int cr = 0; cr < op.q; ++cr) {
+            double a = op.coef[(size_t)(base + cr) * op.S + ((dx + 1) * 3 + (dy + 1)) * op.q + c];
+            acc = crfma(-a, xf[(size_t)(base + cr) * k + j], acc);
+          }
+        }
+      }
+    }
+    if (RESID) {
+      double2 bb = bvec[e];
+      acc = mk(bb.x - acc.x, bb.y - acc.y);
+    }
+    y[e] = acc;
+  }
+}
+
+__global__ void phi_kernel(const double* __restrict__ flow, int nx, int ny, int periodic,
+                           double dx, double dy, int q, double* __restrict__ phi) {
+  int pt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= nx * ny) return;
+  int i = pt / ny, j = pt % ny;
+  Field U{flow + nx * ny, nx, ny, periodic, dx, dy};
+  Field V{flow + 2 * nx * ny, nx, ny, periodic, dx, dy};
+  double a = U.d1x(i, j), b = U.d1y(i, j), c = V.d1x(i, j), d = V.d1y(i, j);
+  double p = sqrt(a * a + b * b + c * c + d * d);
+  for (int cc = 0; cc < q; ++cc) phi[pt * q + cc] = p;
+}
+
+}  // namespace
+
+rr_status launch_assemble(OpDev& d, const rr_grid& g, cudaStream_t st) {
+  AsmParams p;
+  p.kind = g.kind; p.q = d.q; p.nx = d.nx; p.ny = d.ny; p.periodic = d.periodic;
+  p.dx = d.dx; p.dy = d.dy; p.x0 = g.x0; p.x1 = g.x1; p.y0 = g.y0; p.y1 = g.y1;
+  p.re = g.re; p.c2 = (g.kind == RR_ISO_NS2D) ? 1.0 / (g.mach * g.mach) : 0.0;
+  p.smax = g.sponge_max; p.sfrac = g.sponge_frac;
+  int npts = d.nx * d.ny;
+  assemble_kernel<<<(npts + 127) / 128, 128, 0, st>>>(p, d.flow, d.coef);
+  RR_CUDA(cudaGetLastError());
+  return RR_OK;
+}
+
+static int grid_for(size_t total, int threads, int dev) {
+  size_t blocks = (total + threads - 1) / threads;
+  size_t cap = (size_t)num_sms(dev) * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
+                       const double2* x, double2* y, cudaStream_t st) {
+  size_t total = (size_t)F * d.n * k;
+  apply_kernel<false><<<grid_for(total, 256, d.device), 256, 0, st>>>(
+      view(d), shifts, F, k, adjoint, nullptr, x, y);
+  RR_CUDA(cudaGetLastError());
+  return RR_OK;
+}
+
+rr_status launch_residual(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
+                          const double2* b, const double2* x, double2* r, cudaStream_t st) {
+  size_t total = (size_t)F * d.n * k;
+  apply_kernel<true><<<grid_for(total, 256, d.device), 256, 0, st>>>(
+      view(d), shifts, F, k, adjoint, b, x, r);
+  RR_CUDA(cudaGetLastError());
+  return RR_OK;
+}
+
+rr_status launch_phi(const OpDev& d, double* phi, cudaStream_t st) {
+  int npts = d.nx * d.ny;
+  phi_kernel<<<(npts + 127) / 128, 128, 0, st>>>(d.flow, d.nx, d.ny, d.periodic, d.dx, d.dy,
+                                                 d.q, phi);
+  RR_CUDA(cudaGetLastError());
+  return RR_OK;
+}

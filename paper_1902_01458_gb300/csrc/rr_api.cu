@@ -1,0 +1,633 @@
+// C ABI of librr: operator and factor handles, and the host orchestration of
+// Algorithm 1 (Sec. II.B) over the device kernels.  Every step of the path
+// runs on the GPU; the host only sequences launches and, for the iterative
+// refinement of the FP32 factors, reads back residual norms.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rr_internal.cuh"
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+rr_status cuda_status(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? RR_ERR_NOMEM : RR_ERR_CUDA;
+}
+
+static rr_status arg_error(const std::string& msg) {
+  g_err = msg;
+  return RR_ERR_ARG;
+}
+
+int num_sms(int device) {
+  static int cached[64] = {0};
+  if (device < 0 || device >= 64) return 152;
+  if (cached[device] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0)
+      v = 152;
+    cached[device] = v;
+  }
+  return cached[device];
+}
+
+extern "C" const char* rr_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* rr_status_string(rr_status s) {
+  switch (s) {
+    case RR_OK: return "ok";
+    case RR_ERR_ARG: return "invalid argument";
+    case RR_ERR_NOMEM: return "out of device memory";
+    case RR_ERR_SINGULAR: return "singular pivot";
+    case RR_ERR_NOCONV: return "refinement did not converge";
+    case RR_ERR_RANK: return "CholeskyQR breakdown";
+    case RR_ERR_TIMEOUT: return "device wait timed out";
+    case RR_ERR_CUDA: return "CUDA error";
+    case RR_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename P>
+rr_status dalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[128];
+    snprintf(buf, sizeof buf, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    g_err = buf;
+    return RR_ERR_NOMEM;
+  }
+  return RR_OK;
+}
+
+// Sketch workspace carved out of one allocation.
+struct Work {
+  double2 *W1, *W2, *W3, *R64;  // [F][N][k] FP64
+  void *L1, *L2, *L3;           // [F][N][k] factor precision
+  double2 *G, *R1, *R1i, *R2, *R2i, *Rt, *Ul, *Vr;  // [F][k][k]
+  double2* part;                // gram partials
+  double* dpart;                // norm / max partials
+  double *sig, *cond, *bn, *rn; // [F][k] or [F]
+  int *bad, *rank, *sweeps;
+  double2* phase;
+  uint64_t* seeds;
+  int nblk_gram, nblk_col;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Compute the layout (or carve it when base != nullptr); returns total bytes.
+size_t carve(rr_factors* fa, int k, char* base, Work* w) {
+  const int F = fa->F, N = fa->op->d.n;
+  const size_t vec64 = (size_t)F * N * k * sizeof(double2);
+  const size_t veclo = (size_t)F * N * k * fa->csz;
+  const size_t small = (size_t)F * k * k * sizeof(double2);
+  int nblk_gram = std::max(1, std::min(N / 64, std::max(1, 2 * num_sms(fa->op->d.device) / F)));
+  int nblk_col = nblk_gram;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return base ? base + o : nullptr;
+  };
+  Work t;
+  t.W1 = (double2*)take(vec64);
+  t.W2 = (double2*)take(vec64);
+  t.W3 = (double2*)take(vec64);
+  t.R64 = (double2*)take(vec64);
+  t.L1 = take(veclo);
+  t.L2 = take(veclo);
+  t.L3 = take(veclo);
+  t.G = (double2*)take(small);
+  t.R1 = (double2*)take(small);
+  t.R1i = (double2*)take(small);
+  t.R2 = (double2*)take(small);
+  t.R2i = (double2*)take(small);
+  t.Rt = (double2*)take(small);
+  t.Ul = (double2*)take(small);
+  t.Vr = (double2*)take(small);
+  t.part = (double2*)take((size_t)F * nblk_gram * k * k * sizeof(double2));
+  t.dpart = (double*)take((size_t)F * nblk_col * k * (sizeof(double) + sizeof(int)));
+  t.sig = (double*)take((size_t)F * k * sizeof(double));
+  t.cond = (double*)take((size_t)F * sizeof(double));
+  t.bn = (double*)take((size_t)F * k * sizeof(double));
+  t.rn = (double*)take((size_t)F * k * sizeof(double));
+  t.bad = (int*)take((size_t)F * sizeof(int));
+  t.rank = (int*)take((size_t)F * k * sizeof(int));
+  t.sweeps = (int*)take((size_t)F * sizeof(int));
+  t.phase = (double2*)take((size_t)F * k * sizeof(double2));
+  t.seeds = (uint64_t*)take((size_t)F * sizeof(uint64_t));
+  t.nblk_gram = nblk_gram;
+  t.nblk_col = nblk_col;
+  if (w) *w = t;
+  return off;
+}
+
+rr_status get_work(rr_factors* fa, int k, Work* w) {
+  if (k > fa->kmax || fa->ws == nullptr) {
+    if (fa->ws) {
+      cudaStreamSynchronize(fa->stream);
+      cudaFree(fa->ws);
+      fa->ws = nullptr;
+    }
+    size_t bytes = carve(fa, k, nullptr, nullptr);
+    rr_status s = dalloc(reinterpret_cast<char**>(&fa->ws), bytes);
+    if (s != RR_OK) return s;
+    fa->ws_bytes = bytes;
+    fa->kmax = k;
+  }
+  carve(fa, k, reinterpret_cast<char*>(fa->ws), w);
+  return RR_OK;
+}
+
+void info_reset(rr_info* info) {
+  if (!info) return;
+  info->refine_iters = 0;
+  info->refine_residual = 0.0;
+  info->cqr_cond = 0.0;
+  info->cqr_shifted = 0;
+}
+
+// x = A^{-1} b (or A^{-H} b) in FP64 [F][N][k], b != x, with FP64 iterative
+// refinement: x <- x + solve(b - A x) until every column's relative residual
+// is at most tol (tol <= 0: one solve, residual reported only when info).
+rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, double2* x,
+                        double tol, int maxit, Work& w, rr_info* info) {
+  const OpDev& d = fa->op->d;
+  const int F = fa->F;
+  const size_t nel = (size_t)F * d.n * k;
+  cudaStream_t st = fa->stream;
+  const bool lo = fa->prec != RR_FP64;
+  rr_status s;
+  // first solve
+  if (!lo) {
+    if ((s = launch_solve_lo(fa, k, adjoint, b, x, w.L3)) != RR_OK) return s;
+  } else {
+    if ((s = launch_convert_d2f(nel, b, (float2*)w.L1, st)) != RR_OK) return s;
+    if ((s = launch_solve_lo(fa, k, adjoint, w.L1, w.L2, w.L3)) != RR_OK) return s;
+    if ((s = launch_convert_f2d(nel, (const float2*)w.L2, x, 0, st)) != RR_OK) return s;
+  }
+  const bool check = lo || info != nullptr || tol > 0.0;
+  if (!check) return RR_OK;
+  if ((s = launch_colnorm2(F, d.n, k, b, w.dpart, w.nblk_col, w.bn, st)) != RR_OK) return s;
+  std::vector<double> bn((size_t)F * k), rn((size_t)F * k);
+  RR_CUDA(cudaMemcpyAsync(bn.data(), w.bn, bn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  int it = 0;
+  double rel = 0.0;
+  rr_status result = RR_OK;
+  for (;;) {
+    if ((s = launch_residual(d, F, fa->shifts, k, adjoint, b, x, w.R64, st)) != RR_OK) return s;
+    if ((s = launch_colnorm2(F, d.n, k, w.R64, w.dpart, w.nblk_col, w.rn, st)) != RR_OK) return s;
+    RR_CUDA(cudaMemcpyAsync(rn.data(), w.rn, rn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    rel = 0.0;
+    for (size_t e = 0; e < rn.size(); ++e) {
+      double r = bn[e] > 0.0 ? rn[e] / bn[e] : rn[e];
+      if (!(r == r)) r = INFINITY;
+      rel = std::max(rel, r);
+    }
+    if (tol <= 0.0 || rel <= tol) break;
+    if (it >= maxit) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "refinement stopped after %d iterations at relative residual %.3e > %.3e",
+               it, rel, tol);
+      g_err = buf;
+      result = RR_ERR_NOCONV;
+      break;
+    }
+    // correction d = solve(r); x += d
+    if (!lo) {
+      // FP64 factors: the correction lands in L2 (complex double here)
+      if ((s = launch_solve_lo(fa, k, adjoint, w.R64, w.L2, w.L3)) != RR_OK) return s;
+      if ((s = launch_axpy(nel, (const double2*)w.L2, x, st)) != RR_OK) return s;
+    } else {
+      if ((s = launch_convert_d2f(nel, w.R64, (float2*)w.L1, st)) != RR_OK) return s;
+      if ((s = launch_solve_lo(fa, k, adjoint, w.L1, w.L2, w.L3)) != RR_OK) return s;
+      if ((s = launch_convert_f2d(nel, (const float2*)w.L2, x, 1, st)) != RR_OK) return s;
+    }
+    ++it;
+  }
+  if (info) {
+    info->refine_iters = std::max(info->refine_iters, it);
+    info->refine_residual = std::max(info->refine_residual, rel);
+  }
+  return result;
+}
+
+// CholeskyQR2 (shifted CholeskyQR3 on breakdown) of Y in place; R = R2 R1 (R3).
+rr_status cholqr2(rr_factors* fa, int k, double2* Y, double2* Rout, Work& w, rr_info* info) {
+  const int F = fa->F, N = fa->op->d.n;
+  cudaStream_t st = fa->stream;
+  rr_status s;
+  RR_CUDA(cudaMemsetAsync(w.bad, 0, F * sizeof(int), st));
+  if ((s = launch_gram(F, N, k, Y, w.part, w.nblk_gram, w.G, st)) != RR_OK) return s;
+  if ((s = launch_cholesky(F, k, w.G, w.R1, w.R1i, w.bad, 0.0, w.cond, st)) != RR_OK) return s;
+  std::vector<int> bad(F);
+  std::vector<double> cond(F);
+  RR_CUDA(cudaMemcpyAsync(bad.data(), w.bad, F * sizeof(int), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaMemcpyAsync(cond.data(), w.cond, F * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  bool any_bad = false;
+  for (int f = 0; f < F; ++f) any_bad |= bad[f] != 0;
+  int passes = 2;
+  if (any_bad) {
+    // shifted CholeskyQR (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa,
+    // SIAM J. Sci. Comput. 2020): shift 11 (N k + k (k + 1)) u ||Y||^2,
+    // with trace(G) >= ||Y||_2^2, then two plain passes.
+    const double u = std::ldexp(1.0, -53);
+    double shift_rel = 11.0 * ((double)N * k + (double)k * (k + 1)) * u;
+    RR_CUDA(cudaMemsetAsync(w.bad, 0, F * sizeof(int), st));
+    if ((s = launch_cholesky(F, k, w.G, w.R1, w.R1i, w.bad, shift_rel, w.cond, st)) != RR_OK)
+      return s;
+    if (info) info->cqr_shifted = 1;
+    passes = 3;
+  }
+  for (int f = 0; f < F; ++f)
+    if (info) info->cqr_cond = std::max(info->cqr_cond, cond[f]);
+  if ((s = launch_right_mul(F, N, k, Y, w.R1i, Y, st)) != RR_OK) return s;
+  RR_CUDA(cudaMemcpyAsync(w.Rt, w.R1, (size_t)F * k * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  for (int p = 1; p < passes; ++p) {
+    RR_CUDA(cudaMemsetAsync(w.bad, 0, F * sizeof(int), st));
+    if ((s = launch_gram(F, N, k, Y, w.part, w.nblk_gram, w.G, st)) != RR_OK) return s;
+    if ((s = launch_cholesky(F, k, w.G, w.R2, w.R2i, w.bad, 0.0, nullptr, st)) != RR_OK) return s;
+    if ((s = launch_right_mul(F, N, k, Y, w.R2i, Y, st)) != RR_OK) return s;
+    if ((s = launch_small_mul(F, k, w.R2, w.Rt, w.R1, st)) != RR_OK) return s;
+    RR_CUDA(cudaMemcpyAsync(w.Rt, w.R1, (size_t)F * k * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  }
+  RR_CUDA(cudaMemcpyAsync(bad.data(), w.bad, F * sizeof(int), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  for (int f = 0; f < F; ++f)
+    if (bad[f]) {
+      g_err = "CholeskyQR breakdown: the sketch is numerically rank deficient";
+      return RR_ERR_RANK;
+    }
+  if (Rout)
+    RR_CUDA(cudaMemcpyAsync(Rout, w.Rt, (size_t)F * k * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  return RR_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- operator
+extern "C" rr_status rr_create_operator(const rr_grid* g, const rr_baseflow* fl,
+                                        const double* weights, int device, rr_operator** out) {
+  if (!g || !fl || !out) return arg_error("rr_create_operator: null argument");
+  *out = nullptr;
+  if (g->kind != RR_ADVDIFF_SCALAR && g->kind != RR_ISO_NS2D)
+    return arg_error("rr_create_operator: unknown operator kind");
+  if (g->nx < 3 || g->ny < 3) return arg_error("rr_create_operator: nx and ny must be >= 3");
+  const int q = g->kind;
+  if (q * g->ny > 1024) return arg_error("rr_create_operator: block size q*ny must be <= 1024");
+  if (!(g->re > 0)) return arg_error("rr_create_operator: re must be positive");
+  if (g->kind == RR_ISO_NS2D && !(g->mach > 0))
+    return arg_error("rr_create_operator: mach must be positive");
+  if (!(g->x1 > g->x0) || !(g->y1 > g->y0)) return arg_error("rr_create_operator: empty domain");
+  if (g->sponge_max != 0.0 && !(g->sponge_frac > 0.0 && g->sponge_frac <= 0.5))
+    return arg_error("rr_create_operator: sponge_frac must be in (0, 0.5]");
+  if (!fl->u || !fl->v || (g->kind == RR_ISO_NS2D && !fl->rho))
+    return arg_error("rr_create_operator: missing base-flow field");
+  const size_t npts = (size_t)g->nx * g->ny;
+  const size_t N = npts * q;
+  if (N > (size_t)1 << 30) return arg_error("rr_create_operator: too many unknowns");
+  if (weights)
+    for (size_t n = 0; n < N; ++n)
+      if (!(weights[n] > 0.0) || !std::isfinite(weights[n]))
+        return arg_error("rr_create_operator: weights must be positive and finite");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    g_err = "rr_create_operator: no CUDA device";
+    return RR_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return arg_error("rr_create_operator: bad device ordinal");
+  DeviceGuard guard(device);
+  rr_operator* op = new rr_operator();
+  op->grid = *g;
+  OpDev& d = op->d;
+  d.kind = g->kind; d.q = q; d.nx = g->nx; d.ny = g->ny; d.b = q * g->ny; d.n = (int)N;
+  d.periodic = g->periodic_y ? 1 : 0;
+  d.dx = (g->x1 - g->x0) / (g->nx + 1);
+  d.dy = d.periodic ? (g->y1 - g->y0) / g->ny : (g->y1 - g->y0) / (g->ny + 1);
+  d.device = device;
+  d.coef = nullptr; d.wsqrt = nullptr; d.wisqrt = nullptr; d.flow = nullptr;
+  rr_status s;
+  auto fail = [&](rr_status st) {
+    cudaFree(d.coef); cudaFree(d.wsqrt); cudaFree(d.wisqrt); cudaFree(d.flow);
+    delete op;
+    return st;
+  };
+  if ((s = dalloc(&d.coef, N * 9 * q * sizeof(double))) != RR_OK) return fail(s);
+  if ((s = dalloc(&d.flow, 3 * npts * sizeof(double))) != RR_OK) return fail(s);
+  std::vector<double> hf(3 * npts, 1.0);
+  if (fl->rho) std::memcpy(hf.data(), fl->rho, npts * sizeof(double));
+  std::memcpy(hf.data() + npts, fl->u, npts * sizeof(double));
+  std::memcpy(hf.data() + 2 * npts, fl->v, npts * sizeof(double));
+  if (g->kind == RR_ISO_NS2D)
+    for (size_t p = 0; p < npts; ++p)
+      if (!(hf[p] > 0.0)) return fail(arg_error("rr_create_operator: rho must be positive"));
+  cudaError_t e = cudaMemcpy(d.flow, hf.data(), hf.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemcpy flow"));
+  if (weights) {
+    std::vector<double> ws(N), wi(N);
+    for (size_t n = 0; n < N; ++n) {
+      ws[n] = std::sqrt(weights[n]);
+      wi[n] = 1.0 / ws[n];
+    }
+    if ((s = dalloc(&d.wsqrt, N * sizeof(double))) != RR_OK) return fail(s);
+    if ((s = dalloc(&d.wisqrt, N * sizeof(double))) != RR_OK) return fail(s);
+    e = cudaMemcpy(d.wsqrt, ws.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d.wisqrt, wi.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemcpy weights"));
+  }
+  if ((s = launch_assemble(d, *g, 0)) != RR_OK) return fail(s);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(cuda_status(e, "operator assembly"));
+  *out = op;
+  return RR_OK;
+}
+
+extern "C" rr_status rr_destroy_operator(rr_operator* op) {
+  if (!op) return RR_OK;
+  DeviceGuard guard(op->d.device);
+  cudaFree(op->d.coef);
+  cudaFree(op->d.wsqrt);
+  cudaFree(op->d.wisqrt);
+  cudaFree(op->d.flow);
+  delete op;
+  return RR_OK;
+}
+
+extern "C" rr_status rr_operator_dims(const rr_operator* op, int* n, int* b, int* q, int* nx,
+                                      int* ny) {
+  if (!op) return arg_error("rr_operator_dims: null operator");
+  if (n) *n = op->d.n;
+  if (b) *b = op->d.b;
+  if (q) *q = op->d.q;
+  if (nx) *nx = op->d.nx;
+  if (ny) *ny = op->d.ny;
+  return RR_OK;
+}
+
+extern "C" rr_status rr_apply(rr_operator* op, int nshift, const double* shifts, int k, int adjoint,
+                              const void* x, void* y, void* stream) {
+  if (!op || !shifts || !x || !y) return arg_error("rr_apply: null argument");
+  if (nshift < 1 || k < 1) return arg_error("rr_apply: nshift and k must be >= 1");
+  if (x == y) return arg_error("rr_apply: x and y must be distinct");
+  DeviceGuard guard(op->d.device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  double2* sd = nullptr;
+  rr_status s = dalloc(&sd, nshift * sizeof(double2));
+  if (s != RR_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(sd, shifts, nshift * sizeof(double2), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) { cudaFree(sd); return cuda_status(e, "rr_apply shifts"); }
+  s = launch_apply(op->d, nshift, sd, k, adjoint, (const double2*)x, (double2*)y, st);
+  e = cudaStreamSynchronize(st);
+  cudaFree(sd);
+  if (s != RR_OK) return s;
+  if (e != cudaSuccess) return cuda_status(e, "rr_apply");
+  return RR_OK;
+}
+
+extern "C" rr_status rr_phi(rr_operator* op, double* phi, void* stream) {
+  if (!op || !phi) return arg_error("rr_phi: null argument");
+  DeviceGuard guard(op->d.device);
+  return launch_phi(op->d, phi, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------------------ factors
+extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts, rr_precision prec,
+                               void* stream, rr_factors** out) {
+  if (!op || !shifts || !out) return arg_error("rr_factor: null argument");
+  *out = nullptr;
+  if (nshift < 1 || nshift > 65535) return arg_error("rr_factor: nshift must be in [1, 65535]");
+  if (prec != RR_FP64 && prec != RR_FP32) return arg_error("rr_factor: unknown precision");
+  for (int f = 0; f < 2 * nshift; ++f)
+    if (!std::isfinite(shifts[f])) return arg_error("rr_factor: shifts must be finite");
+  DeviceGuard guard(op->d.device);
+  const OpDev& d = op->d;
+  rr_factors* fa = new rr_factors();
+  std::memset(fa, 0, sizeof(*fa));
+  fa->op = op;
+  fa->F = nshift;
+  fa->prec = prec;
+  fa->stream = reinterpret_cast<cudaStream_t>(stream);
+  fa->csz = prec == RR_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t bb = (size_t)d.b * d.b;
+  rr_status s;
+  auto fail = [&](rr_status st) {
+    rr_destroy_factors(fa);
+    return st;
+  };
+  if ((s = dalloc(&fa->G, (size_t)nshift * d.nx * bb * fa->csz)) != RR_OK) return fail(s);
+  if ((s = dalloc(&fa->X, (size_t)nshift * std::max(1, d.nx - 1) * bb * fa->csz)) != RR_OK) return fail(s);
+  if ((s = dalloc(&fa->M, (size_t)nshift * bb * fa->csz)) != RR_OK) return fail(s);
+  if ((s = dalloc(&fa->Bbuf, (size_t)nshift * 32 * d.b * fa->csz)) != RR_OK) return fail(s);
+  if ((s = dalloc(&fa->perm, (size_t)nshift * d.b * sizeof(int))) != RR_OK) return fail(s);
+  if ((s = dalloc(&fa->ipiv, (size_t)nshift * 32 * sizeof(int))) != RR_OK) return fail(s);
+  if ((s = dalloc(&fa->flag, (size_t)nshift * sizeof(int))) != RR_OK) return fail(s);
+  if ((s = dalloc(&fa->shifts, (size_t)nshift * sizeof(double2))) != RR_OK) return fail(s);
+  fa->shifts_h = new double2[nshift];
+  for (int f = 0; f < nshift; ++f) fa->shifts_h[f] = make_double2(shifts[2 * f], shifts[2 * f + 1]);
+  cudaStream_t st = fa->stream;
+  cudaError_t e = cudaMemcpyAsync(fa->shifts, fa->shifts_h, nshift * sizeof(double2),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "rr_factor shifts"));
+  e = cudaMemsetAsync(fa->flag, 0, nshift * sizeof(int), st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "rr_factor flags"));
+  if ((s = launch_factor(fa)) != RR_OK) return fail(s);
+  std::vector<int> flags(nshift);
+  e = cudaMemcpyAsync(flags.data(), fa->flag, nshift * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "rr_factor"));
+  *out = fa;
+  for (int f = 0; f < nshift; ++f)
+    if (flags[f]) {
+      char buf[128];
+      snprintf(buf, sizeof buf, "rr_factor: exact zero pivot for shift %d (%g%+gi)", f,
+               fa->shifts_h[f].x, fa->shifts_h[f].y);
+      g_err = buf;
+      return RR_ERR_SINGULAR;
+    }
+  return RR_OK;
+}
+
+extern "C" rr_status rr_destroy_factors(rr_factors* fa) {
+  if (!fa) return RR_OK;
+  DeviceGuard guard(fa->op->d.device);
+  if (fa->stream) cudaStreamSynchronize(fa->stream);
+  cudaFree(fa->G);
+  cudaFree(fa->X);
+  cudaFree(fa->M);
+  cudaFree(fa->Bbuf);
+  cudaFree(fa->perm);
+  cudaFree(fa->ipiv);
+  cudaFree(fa->flag);
+  cudaFree(fa->shifts);
+  cudaFree(fa->ws);
+  delete[] fa->shifts_h;
+  delete fa;
+  return RR_OK;
+}
+
+extern "C" rr_status rr_factors_dims(const rr_factors* fa, int* nshift, int* prec) {
+  if (!fa) return arg_error("rr_factors_dims: null factors");
+  if (nshift) *nshift = fa->F;
+  if (prec) *prec = fa->prec;
+  return RR_OK;
+}
+
+static rr_status check_k(rr_factors* fa, int k, const char* who) {
+  if (!fa) return arg_error(std::string(who) + ": null factors");
+  if (k < 1 || k > 64) return arg_error(std::string(who) + ": k must be in [1, 64]");
+  if (k > fa->op->d.n) return arg_error(std::string(who) + ": k must not exceed N");
+  return RR_OK;
+}
+
+extern "C" rr_status rr_solve(rr_factors* fa, int k, int adjoint, const void* b, void* x,
+                              double refine_tol, int max_refine, rr_info* info) {
+  rr_status s = check_k(fa, k, "rr_solve");
+  if (s != RR_OK) return s;
+  if (!b || !x) return arg_error("rr_solve: null vector");
+  if (b == x) return arg_error("rr_solve: b and x must be distinct");
+  if (max_refine < 0) return arg_error("rr_solve: max_refine must be >= 0");
+  DeviceGuard guard(fa->op->d.device);
+  info_reset(info);
+  Work w;
+  if ((s = get_work(fa, k, &w)) != RR_OK) return s;
+  const OpDev& d = fa->op->d;
+  const int F = fa->F;
+  const size_t bytes = (size_t)F * d.n * k * sizeof(double2);
+  cudaStream_t st = fa->stream;
+  // R b = W^{1/2} A^{-1} W^{-1/2} b ;  R^H b = W^{-1/2} A^{-H} W^{1/2} b
+  RR_CUDA(cudaMemcpyAsync(w.W2, b, bytes, cudaMemcpyDeviceToDevice, st));
+  if ((s = launch_scale_rows(F, d.n, k, adjoint ? d.wsqrt : d.wisqrt, w.W2, st)) != RR_OK) return s;
+  s = solve_refined(fa, k, adjoint, w.W2, (double2*)x, refine_tol, max_refine, w, info);
+  if (s != RR_OK && s != RR_ERR_NOCONV) return s;
+  rr_status s2 = launch_scale_rows(F, d.n, k, adjoint ? d.wisqrt : d.wsqrt, (double2*)x, st);
+  if (s2 != RR_OK) return s2;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "rr_solve");
+  return s;
+}
+
+extern "C" rr_status rr_sketch(rr_factors* fa, int k, const uint64_t* seeds, const double* phi,
+                               double refine_tol, int max_refine, void* V, double* sigma_halko,
+                               rr_info* info) {
+  rr_status s = check_k(fa, k, "rr_sketch");
+  if (s != RR_OK) return s;
+  if (!seeds || !V || !sigma_halko) return arg_error("rr_sketch: null argument");
+  if (max_refine < 0) return arg_error("rr_sketch: max_refine must be >= 0");
+  DeviceGuard guard(fa->op->d.device);
+  info_reset(info);
+  Work w;
+  if ((s = get_work(fa, k, &w)) != RR_OK) return s;
+  const OpDev& d = fa->op->d;
+  const int F = fa->F, N = d.n;
+  const size_t bytes = (size_t)F * N * k * sizeof(double2);
+  cudaStream_t st = fa->stream;
+  rr_status conv = RR_OK;
+  RR_CUDA(cudaMemcpyAsync(w.seeds, seeds, F * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  // Omega' = W^{-1/2} diag(phi) randn  (first step, Eq. 9)
+  if ((s = launch_philox(F, N, k, w.seeds, phi, d.wisqrt, w.W1, st)) != RR_OK) return s;
+  // Y = W^{1/2} A^{-1} Omega'  (second step)
+  s = solve_refined(fa, k, 0, w.W1, w.W2, refine_tol, max_refine, w, info);
+  if (s == RR_ERR_NOCONV) conv = s; else if (s != RR_OK) return s;
+  if ((s = launch_scale_rows(F, N, k, d.wsqrt, w.W2, st)) != RR_OK) return s;
+  // Q = qr(Y)  (third step)
+  if ((s = cholqr2(fa, k, w.W2, nullptr, w, info)) != RR_OK) return s;
+  // B^H = W^{-1/2} A^{-H} W^{1/2} Q  (fourth step)
+  RR_CUDA(cudaMemcpyAsync(w.W1, w.W2, bytes, cudaMemcpyDeviceToDevice, st));
+  if ((s = launch_scale_rows(F, N, k, d.wsqrt, w.W1, st)) != RR_OK) return s;
+  s = solve_refined(fa, k, 1, w.W1, w.W3, refine_tol, max_refine, w, info);
+  if (s == RR_ERR_NOCONV) conv = s; else if (s != RR_OK) return s;
+  if ((s = launch_scale_rows(F, N, k, d.wisqrt, w.W3, st)) != RR_OK) return s;
+  // svd(B): B^H = Q_B R_B, R_B = Ul S Vr^H  =>  V = Q_B Ul, sigma = S  (fifth step)
+  if ((s = cholqr2(fa, k, w.W3, w.R2i, w, info)) != RR_OK) return s;
+  if ((s = launch_jacobi_svd(F, k, w.R2i, w.sig, w.Ul, w.Vr, w.sweeps, st)) != RR_OK) return s;
+  if ((s = launch_right_mul(F, N, k, w.W3, w.Ul, (double2*)V, st)) != RR_OK) return s;
+  RR_CUDA(cudaMemcpyAsync(sigma_halko, w.sig, (size_t)F * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  return conv;
+}
+
+extern "C" rr_status rr_modes(rr_factors* fa, int k, void* V, void* U, double* sigma,
+                              int orthogonalize, double refine_tol, int max_refine, rr_info* info) {
+  rr_status s = check_k(fa, k, "rr_modes");
+  if (s != RR_OK) return s;
+  if (!V || !U || !sigma) return arg_error("rr_modes: null argument");
+  if (U == V) return arg_error("rr_modes: U and V must be distinct");
+  if (max_refine < 0) return arg_error("rr_modes: max_refine must be >= 0");
+  DeviceGuard guard(fa->op->d.device);
+  info_reset(info);
+  Work w;
+  if ((s = get_work(fa, k, &w)) != RR_OK) return s;
+  const OpDev& d = fa->op->d;
+  const int F = fa->F, N = d.n;
+  const size_t bytes = (size_t)F * N * k * sizeof(double2);
+  cudaStream_t st = fa->stream;
+  rr_status conv = RR_OK;
+  // U Sigma = W^{1/2} A^{-1} W^{-1/2} V  (Eq. 8)
+  RR_CUDA(cudaMemcpyAsync(w.W1, V, bytes, cudaMemcpyDeviceToDevice, st));
+  if ((s = launch_scale_rows(F, N, k, d.wisqrt, w.W1, st)) != RR_OK) return s;
+  s = solve_refined(fa, k, 0, w.W1, w.W2, refine_tol, max_refine, w, info);
+  if (s == RR_ERR_NOCONV) conv = s; else if (s != RR_OK) return s;
+  if ((s = launch_scale_rows(F, N, k, d.wsqrt, w.W2, st)) != RR_OK) return s;
+  if (!orthogonalize) {
+    // sigma_j = ||(U Sigma)_j||, u_j = (U Sigma)_j / sigma_j
+    if ((s = launch_colnorm2(F, N, k, w.W2, w.dpart, w.nblk_col, sigma, st)) != RR_OK) return s;
+    if ((s = launch_col_scale(F, N, k, w.W2, sigma, (double2*)U, st)) != RR_OK) return s;
+  } else {
+    // optional: svd(U Sigma) = U S Vt^H via CholeskyQR2 + Jacobi; V <- V Vt
+    if ((s = cholqr2(fa, k, w.W2, w.R2i, w, info)) != RR_OK) return s;
+    if ((s = launch_jacobi_svd(F, k, w.R2i, sigma, w.Ul, w.Vr, w.sweeps, st)) != RR_OK) return s;
+    if ((s = launch_right_mul(F, N, k, w.W2, w.Ul, (double2*)U, st)) != RR_OK) return s;
+    if ((s = launch_right_mul(F, N, k, (const double2*)V, w.Vr, (double2*)V, st)) != RR_OK) return s;
+  }
+  if ((s = launch_finish_modes(F, N, k, (double2*)U, (double2*)V, sigma, w.W1, w.W3, w.dpart,
+                               w.nblk_col, w.rank, w.phase, st)) != RR_OK)
+    return s;
+  RR_CUDA(cudaStreamSynchronize(st));
+  return conv;
+}
+
+extern "C" rr_status rr_gaussian(int nshift, int n, int k, const uint64_t* seeds, const double* phi,
+                                 void* omega, void* stream) {
+  if (!seeds || !omega) return arg_error("rr_gaussian: null argument");
+  if (nshift < 1 || n < 1 || k < 1) return arg_error("rr_gaussian: sizes must be >= 1");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint64_t* sd = nullptr;
+  rr_status s = dalloc(&sd, nshift * sizeof(uint64_t));
+  if (s != RR_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(sd, seeds, nshift * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) s = launch_philox(nshift, n, k, sd, phi, nullptr, (double2*)omega, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(sd);
+  if (e != cudaSuccess) return cuda_status(e, "rr_gaussian");
+  return s;
+}

@@ -1,0 +1,183 @@
+// Internal declarations shared by the CUDA translation units of librr.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "rr.h"
+
+// ------------------------------------------------------------ complex math
+// Interleaved complex in the CUDA vector types: .x = re, .y = im.
+template <typename T> struct cplx_t;
+template <> struct cplx_t<double> { using type = double2; };
+template <> struct cplx_t<float> { using type = float2; };
+template <typename T> using C_t = typename cplx_t<T>::type;
+
+__host__ __device__ __forceinline__ double2 mk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ float2 mk(float r, float i) { return make_float2(r, i); }
+template <typename C> __device__ __forceinline__ C czero();
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cneg(C a) { return mk(-a.x, -a.y); }
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// c + a*b
+template <typename C> __device__ __forceinline__ C cfma(C a, C b, C c) {
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+// c + conj(a)*b
+template <typename C> __device__ __forceinline__ C cfmac(C a, C b, C c) {
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(-a.y, b.x, c.y);
+  return c;
+}
+// c + r*b (r real)
+template <typename C, typename R> __device__ __forceinline__ C crfma(R r, C b, C c) {
+  c.x = fma(r, b.x, c.x);
+  c.y = fma(r, b.y, c.y);
+  return c;
+}
+template <typename C> __device__ __forceinline__ auto cabs2(C a) -> decltype(a.x) { return a.x * a.x + a.y * a.y; }
+template <typename C> __device__ __forceinline__ C cinv(C a) {
+  auto d = a.x * a.x + a.y * a.y;
+  return mk(a.x / d, -a.y / d);
+}
+template <typename To, typename From> __device__ __forceinline__ To ccast(From a);
+template <> __device__ __forceinline__ double2 ccast<double2, double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 ccast<float2, float2>(float2 a) { return a; }
+template <> __device__ __forceinline__ float2 ccast<float2, double2>(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+template <> __device__ __forceinline__ double2 ccast<double2, float2>(float2 a) {
+  return make_double2((double)a.x, (double)a.y);
+}
+
+// ---------------------------------------------------------- operator data
+// Stencil of L: for every unknown row n, S = 9*q real coefficients
+// coef[n*S + ((dx+1)*3 + (dy+1))*q + c'] = L[n, ((ix+dx)*ny + iy+dy)*q + c'],
+// zero where the neighbour is a Dirichlet ghost node.
+struct OpDev {
+  int kind, q, nx, ny, b, n, periodic;
+  double* coef;      // [N][9q]
+  double* wsqrt;     // [N] W^{1/2} or nullptr (identity)
+  double* wisqrt;    // [N] W^{-1/2} or nullptr
+  double* flow;      // [3][nx*ny] rho, U, V
+  double dx, dy;
+  int device;
+};
+
+struct rr_operator {
+  OpDev d;
+  rr_grid grid;
+};
+
+// Device-side view of the operator passed by value to kernels.
+struct OpView {
+  const double* coef;
+  int q, nx, ny, b, n, periodic, S;
+};
+
+inline OpView view(const OpDev& d) {
+  OpView v;
+  v.coef = d.coef;
+  v.q = d.q; v.nx = d.nx; v.ny = d.ny; v.b = d.b; v.n = d.n;
+  v.periodic = d.periodic; v.S = 9 * d.q;
+  return v;
+}
+
+// y index of a neighbour; returns -1 for a Dirichlet ghost.
+__device__ __forceinline__ int nbr_y(int iy, int dy, int ny, int periodic) {
+  int j = iy + dy;
+  if (periodic) return (j + ny) % ny;
+  return (j < 0 || j >= ny) ? -1 : j;
+}
+
+// ------------------------------------------------------------- factors
+struct rr_factors {
+  rr_operator* op;
+  int F;
+  int prec;          // rr_precision
+  cudaStream_t stream;
+  size_t csz;        // bytes of one complex element of the factors
+  void* G;           // [F][nx][b][b]   inverse of each Schur block
+  void* X;           // [F][nx-1][b][b] X_i = G_i C_i
+  void* M;           // [F][b][b] work matrix
+  void* Bbuf;        // [F][32][b] saved pivot rows of the current panel
+  int* perm;         // [F][b]
+  int* ipiv;         // [F][32]
+  int* flag;         // [F] singular-pivot flags
+  double2* shifts;   // [F] device
+  double2* shifts_h; // [F] host copy
+  // workspace for the sketch (allocated lazily, sized for kmax)
+  int kmax;
+  void* ws;          // one allocation, carved below
+  size_t ws_bytes;
+};
+
+// ------------------------------------------------------------ error state
+void set_error(const std::string& msg);
+rr_status cuda_status(cudaError_t e, const char* what);
+#define RR_CUDA(call)                                             \
+  do {                                                            \
+    cudaError_t _e = (call);                                      \
+    if (_e != cudaSuccess) return cuda_status(_e, #call);         \
+  } while (0)
+
+// ------------------------------------------------------- kernel launchers
+// operator.cu
+rr_status launch_assemble(OpDev& d, const rr_grid& g, cudaStream_t st);
+rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
+                       const double2* x, double2* y, cudaStream_t st);
+rr_status launch_residual(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
+                          const double2* b, const double2* x, double2* r, cudaStream_t st);
+rr_status launch_phi(const OpDev& d, double* phi, cudaStream_t st);
+
+// factor.cu
+rr_status launch_factor(rr_factors* f);
+int factor_panel_width(int prec, int b);
+
+// sweep.cu: x = A^{-1} b or A^{-H} b with the factors in precision T.
+// b and x are [F][N][k] in the factor precision; tmp same size (adjoint only).
+rr_status launch_solve_lo(rr_factors* f, int k, int adjoint, const void* b, void* x, void* tmp);
+
+// dense.cu
+rr_status launch_philox(int F, int N, int k, const uint64_t* seeds_dev, const double* phi,
+                        const double* wisqrt, double2* out, cudaStream_t st);
+rr_status launch_scale_rows(int F, int N, int k, const double* w, double2* x, cudaStream_t st);
+rr_status launch_convert_d2f(size_t n, const double2* in, float2* out, cudaStream_t st);
+rr_status launch_convert_f2d(size_t n, const float2* in, double2* out, int accumulate,
+                             cudaStream_t st);
+rr_status launch_colnorm2(int F, int N, int k, const double2* x, double* part, int nblk,
+                          double* out, cudaStream_t st);
+rr_status launch_gram(int F, int N, int k, const double2* Y, double2* part, int nblk,
+                      double2* G, cudaStream_t st);
+rr_status launch_cholesky(int F, int k, const double2* G, double2* R, double2* Rinv,
+                          int* bad, double shift_rel, double* cond, cudaStream_t st);
+rr_status launch_right_mul(int F, int N, int k, const double2* Y, const double2* S,
+                           double2* out, cudaStream_t st);
+rr_status launch_small_mul(int F, int k, const double2* A, const double2* B, double2* C,
+                           cudaStream_t st);
+rr_status launch_jacobi_svd(int F, int k, const double2* R, double* sigma, double2* Ul,
+                            double2* Vr, int* sweeps, cudaStream_t st);
+rr_status launch_col_scale(int F, int N, int k, const double2* in, const double* sigma,
+                           double2* out, cudaStream_t st);
+rr_status launch_finish_modes(int F, int N, int k, double2* U, double2* V, double* sigma,
+                              double2* tmpU, double2* tmpV, double* part, int nblk,
+                              int* rank, double2* phase, cudaStream_t st);
+
+rr_status launch_axpy(size_t n, const double2* d, double2* x, cudaStream_t st);
+
+int num_sms(int device);

@@ -1,0 +1,194 @@
+// Block forward/back sweeps with the stored factors: the linear solves of
+// Algorithm 1 (Sec. II.B, second, fourth and sixth steps), all reusing the
+// one factorisation of s I - L (Sec. III.A).
+//
+// Normal solve (s I - L) y = f:
+//   forward  z_0 = G_0 f_0,     z_i = G_i (f_i + L_{i,i-1} z_{i-1})
+//   backward y_{n-1} = z_{n-1}, y_i = z_i - X_i y_{i+1}
+// Adjoint solve (s I - L)^H w = g:
+//   forward  h_0 = g_0,         h_{i+1} = g_{i+1} - X_i^H h_i
+//   backward w_{n-1} = G^H h,   w_i = G_i^H (h_i + L_{i+1,i}^T w_{i+1})
+// Each step is a dense (b x b) x (b x k) product streamed from HBM; the
+// sparse coupling term is rebuilt per tile while the right-hand side chunk is
+// staged in shared memory.  One launch per streamwise column covers all F
+// problems of the batch.
+#include <algorithm>
+
+#include "rr_internal.cuh"
+
+namespace {
+
+constexpr int SW_THREADS = 256;
+constexpr int SW_OUT = 4;    // outputs per thread: RT * kp = 1024
+constexpr int SW_KC = 32;    // chunk of the contraction dimension
+
+enum { FWD = 0, BWD = 1, ADJ_FWD = 2, ADJ_BWD = 3 };
+
+__device__ __forceinline__ int slotv(int dx, int dy) { return (dx + 1) * 3 + (dy + 1); }
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(SW_THREADS)
+sweep_step_kernel(OpView op, int i, int k, int kp, int RT, const C_t<T>* __restrict__ Mat,
+                  size_t mstride, const C_t<T>* in, C_t<T>* out) {
+  using C = C_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Ms = reinterpret_cast<C*>(smem_raw);   // [RT][KC+1]
+  C* Ts = Ms + RT * (SW_KC + 1);            // [KC][kp]
+  const int b = op.b, q = op.q;
+  const int f = blockIdx.y;
+  const int r0 = blockIdx.x * RT;
+  const size_t NK = (size_t)op.n * k;
+  const C* Mf = Mat + (size_t)f * mstride;
+  const C* inf = in + (size_t)f * NK;
+  C* outf = out + (size_t)f * NK;
+  const int ob = (MODE == ADJ_FWD) ? i + 1 : i;  // output column block
+  const int tb = (MODE == BWD) ? i + 1 : i;      // block index of the staged rhs
+  const int tid = threadIdx.x;
+
+  C acc[SW_OUT];
+#pragma unroll
+  for (int t = 0; t < SW_OUT; ++t) acc[t] = czero<C>();
+
+  for (int m0 = 0; m0 < b; m0 += SW_KC) {
+    // stage the rhs chunk Ts[mm][j] for rows m0..m0+KC of block tb
+    for (int e = tid; e < SW_KC * kp; e += SW_THREADS) {
+      int mm = e / kp, j = e - mm * kp;
+      int m = m0 + mm;
+      C v = czero<C>();
+      if (m < b && j < k) {
+        size_t row = (size_t)tb * b + m;
+        if (MODE == FWD) {
+          v = inf[row * k + j];
+          if (i > 0) {
+            int iy = m / q;
+            const double* cf = op.coef + row * op.S;
+            for (int dy = -1; dy <= 1; ++dy) {
+              int jy = nbr_y(iy, dy, op.ny, op.periodic);
+              if (jy < 0) continue;
+              for (int cp = 0; cp < q; ++cp) {
+                T a = (T)cf[slotv(-1, dy) * q + cp];
+                if (a != (T)0)
+                  v = crfma(a, outf[((size_t)(i - 1) * b + jy * q + cp) * k + j], v);
+              }
+            }
+          }
+        } else if (MODE == BWD || MODE == ADJ_FWD) {
+          v = outf[row * k + j];
+        } else {  // ADJ_BWD
+          v = inf[row * k + j];
+          if (i + 1 < op.nx) {
+            int iym = m / q, cm = m - iym * q;
+            for (int dy = -1; dy <= 1; ++dy) {
+              int iyr = nbr_y(iym, -dy, op.ny, op.periodic);
+              if (iyr < 0) continue;
+              for (int cr = 0; cr < q; ++cr) {
+                size_t rrow = (size_t)(i + 1) * b + iyr * q + cr;
+                T a = (T)op.coef[rrow * op.S + slotv(-1, dy) * q + cm];
+                if (a != (T)0) v = crfma(a, outf[rrow * k + j], v);
+              }
+            }
+          }
+        }
+      }
+      Ts[mm * kp + j] = v;
+    }
+    // stage the matrix tile Ms[rr][mm] = op(Mat)[r0+rr][m0+mm]
+    if (MODE == FWD || MODE == BWD) {
+      for (int e = tid; e < RT * SW_KC; e += SW_THREADS) {
+        int rr = e / SW_KC, mm = e - rr * SW_KC;
+        int r = r0 + rr, m = m0 + mm;
+        Ms[rr * (SW_KC + 1) + mm] = (r < b && m < b) ? Mf[(size_t)r * b + m] : czero<C>();
+      }
+    } else {
+      for (int e = tid; e < RT * SW_KC; e += SW_THREADS) {
+        int mm = e / RT, rr = e - mm * RT;
+        int r = r0 + rr, m = m0 + mm;
+        Ms[rr * (SW_KC + 1) + mm] =
+            (r < b && m < b) ? cconj(Mf[(size_t)m * b + r]) : czero<C>();
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < SW_OUT; ++t) {
+      int o = tid + t * SW_THREADS;
+      int rr = o / kp, j = o - rr * kp;
+      const C* mrow = Ms + rr * (SW_KC + 1);
+      C a = acc[t];
+#pragma unroll 8
+      for (int mm = 0; mm < SW_KC; ++mm) a = cfma(mrow[mm], Ts[mm * kp + j], a);
+      acc[t] = a;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int t = 0; t < SW_OUT; ++t) {
+    int o = tid + t * SW_THREADS;
+    int rr = o / kp, j = o - rr * kp;
+    int r = r0 + rr;
+    if (r >= b || j >= k || rr >= RT) continue;
+    size_t idx = ((size_t)ob * b + r) * k + j;
+    if (MODE == FWD || MODE == ADJ_BWD) {
+      outf[idx] = acc[t];
+    } else {
+      outf[idx] = csub(outf[idx], acc[t]);
+    }
+  }
+}
+
+template <typename T, int MODE>
+rr_status step(rr_factors* fa, int i, int k, int kp, int RT, const C_t<T>* Mat, size_t mstride,
+               const C_t<T>* in, C_t<T>* out) {
+  const OpDev& d = fa->op->d;
+  size_t smem = ((size_t)RT * (SW_KC + 1) + (size_t)SW_KC * kp) * sizeof(C_t<T>);
+  static bool attr_set = false;
+  if (!attr_set) {
+    RR_CUDA(cudaFuncSetAttribute(sweep_step_kernel<T, MODE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    attr_set = true;
+  }
+  dim3 grid((d.b + RT - 1) / RT, fa->F);
+  sweep_step_kernel<T, MODE><<<grid, SW_THREADS, smem, fa->stream>>>(view(d), i, k, kp, RT, Mat,
+                                                                    mstride, in, out);
+  return RR_OK;
+}
+
+template <typename T>
+rr_status solve_impl(rr_factors* fa, int k, int adjoint, const void* bv, void* xv, void* tmpv) {
+  using C = C_t<T>;
+  const OpDev& d = fa->op->d;
+  const int b = d.b, nx = d.nx;
+  int kp = 8;
+  while (kp < k) kp <<= 1;
+  const int RT = (SW_THREADS * SW_OUT) / kp;
+  const size_t bb = (size_t)b * b;
+  const C* G = reinterpret_cast<const C*>(fa->G);
+  const C* X = reinterpret_cast<const C*>(fa->X);
+  const size_t gstride = (size_t)nx * bb;
+  const size_t xstride = (size_t)(nx > 1 ? nx - 1 : 1) * bb;
+  const C* bin = reinterpret_cast<const C*>(bv);
+  C* x = reinterpret_cast<C*>(xv);
+  rr_status s;
+  if (!adjoint) {
+    for (int i = 0; i < nx; ++i)
+      if ((s = step<T, FWD>(fa, i, k, kp, RT, G + i * bb, gstride, bin, x)) != RR_OK) return s;
+    for (int i = nx - 2; i >= 0; --i)
+      if ((s = step<T, BWD>(fa, i, k, kp, RT, X + i * bb, xstride, bin, x)) != RR_OK) return s;
+  } else {
+    C* h = reinterpret_cast<C*>(tmpv);
+    RR_CUDA(cudaMemcpyAsync(h, bin, (size_t)fa->F * d.n * k * sizeof(C),
+                            cudaMemcpyDeviceToDevice, fa->stream));
+    for (int i = 0; i + 1 < nx; ++i)
+      if ((s = step<T, ADJ_FWD>(fa, i, k, kp, RT, X + i * bb, xstride, h, h)) != RR_OK) return s;
+    for (int i = nx - 1; i >= 0; --i)
+      if ((s = step<T, ADJ_BWD>(fa, i, k, kp, RT, G + i * bb, gstride, h, x)) != RR_OK) return s;
+  }
+  RR_CUDA(cudaGetLastError());
+  return RR_OK;
+}
+
+}  // namespace
+
+rr_status launch_solve_lo(rr_factors* fa, int k, int adjoint, const void* b, void* x, void* tmp) {
+  if (fa->prec == RR_FP64) return solve_impl<double>(fa, k, adjoint, b, x, tmp);
+  return solve_impl<float>(fa, k, adjoint, b, x, tmp);
+}
