@@ -1,0 +1,438 @@
+#!/usr/bin/env python3
+"""Throughput of randomized resolvent analysis on one GB300 (or N, sharded).
+
+Workload: linearised isothermal Navier-Stokes (rho, u, v) about the synthetic
+separated base flow (tanh shear layer + Gaussian recirculation bubble),
+Re = 500, M = 0.3, sponge on the outer 10 %, grid 512 x 256 (N = 393,216,
+block 768), 64 frequencies log-spaced in [0.1, 5], k = 32 base-flow-weighted
+Gaussian columns (Eq. 9).  One step = Algorithm 1 for a batch of F
+frequencies: block factorisation (complex FP32), sketch + FP64 refinement to
+residual <= 1e-10, FP64 CholeskyQR2, adjoint solve, small SVD, recovery
+solve.  Synthetic data; the factors (~4.8 GB per frequency) exceed L2, so no
+flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+HBM_PEAK_GBS = 6800.0       # profiling-recipe fallback (no MEASURED_PEAKS.json)
+BF16_PEAK_TFLOPS = 1900.0   # fallback burst figure
+SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+FP32_ALU_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12  # 80.5
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--batch", type=int, default=16, help="frequencies per step per GPU")
+    p.add_argument("--fp64-batch", type=int, default=2)
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--nx", type=int, default=512)
+    p.add_argument("--ny", type=int, default=256)
+    p.add_argument("--k", type=int, default=32)
+    p.add_argument("--roofline-class", default="update")
+    p.add_argument("--breakdown", action="store_true",
+                   help="one extra profiled step with every kernel class timed")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return (float(d.get("hbm_gbs", HBM_PEAK_GBS)),
+                    float(d.get("bf16_tflops", BF16_PEAK_TFLOPS)), "measured")
+        except Exception:
+            pass
+    return HBM_PEAK_GBS, BF16_PEAK_TFLOPS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, dev=None):
+    if pg is not None:
+        if dev is not None:
+            pg.barrier(device_ids=[dev])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, x: float, device) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def batch_for(step, rank, world, F, omegas, seed0):
+    """Frequencies and seeds of one step on one rank (weak scaling shards)."""
+    base = (step * world + rank) * F
+    idx = [(base + j) % len(omegas) for j in range(F)]
+    return 1j * omegas[idx], [seed0 + i for i in idx], idx
+
+
+def update_flops_per_step(b, nx, NB, F):
+    tot = 0
+    for k0 in range(0, b, NB):
+        nbk = min(NB, b - k0)
+        tot += 8 * (b - nbk) ** 2 * nbk
+    return tot * nx * F
+
+
+def panel_width(prec_bytes, b):
+    cap = 227 * 1024 - 2048
+    for nb in (32, 16, 8):
+        if b * nb * prec_bytes + 3 * nb * (nb + 1) * prec_bytes <= cap:
+            return nb
+    return 8
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(grid_full, k, nx_sample, omega, seed):
+    """Time the FP64 oracle (banded LAPACK LU, Householder QR, LAPACK SVD) on
+    the first nx_sample streamwise columns of the workload's grid (same block
+    size), returning seconds; its cost is linear in nx."""
+    from oracle import operator as op
+    from oracle import resolvent as rs
+    g = W.Grid(kind=grid_full.kind, nx=nx_sample, ny=grid_full.ny,
+               x0=grid_full.x0, x1=grid_full.x0 + (grid_full.x1 - grid_full.x0)
+               * (nx_sample + 1) / (grid_full.nx + 1),
+               y0=grid_full.y0, y1=grid_full.y1, re=grid_full.re, mach=grid_full.mach,
+               sponge_max=grid_full.sponge_max, sponge_frac=grid_full.sponge_frac)
+    flow = W.shear_bubble_flow(g)
+    L = op.assemble(g, flow)
+    phi = op.phi(g, flow)
+    t0 = time.perf_counter()
+    rs.randomized(L, 1j * omega, k, seed, phi=phi, method="banded")
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = W.config_mixed()
+    g = W.ns_grid(args.nx, args.ny)
+    nx_s = 16
+    times = []
+    for s in range(args.warmup + args.steps):
+        t = cpu_oracle_sample(g, args.k, nx_s, float(wl.omegas[s % len(wl.omegas)]), 1000 + s)
+        if s >= args.warmup:
+            times.append(t)
+    per_freq = statistics.mean(times) * (g.nx / nx_s)
+    value = 1.0 / per_freq
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": "resolvent frequencies/sec at N=393,216, k=32",
+        "value": value, "unit": "frequencies/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_freq * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"ns2d-{g.nx}x{g.ny}-k{args.k}", "N": g.n, "k": args.k,
+                   "block": g.b, "precision": "fp64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "frequencies/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"one frequency per step on the first {nx_s} of {g.nx} "
+                                   f"streamwise columns (block {g.b}), banded LAPACK LU, "
+                                   f"time scaled x{g.nx // nx_s} (cost linear in nx)"},
+        "e2e": {"value": value, "unit": "frequencies/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_1902_01458_gb300 import build as rrbuild
+    if rank == 0:
+        rrbuild.build()
+    barrier(pg, local)
+    rrbuild.build()
+    import paper_1902_01458_gb300 as rr
+    from paper_1902_01458_gb300 import _lib
+    rr.load()
+
+    wl = W.config_mixed()
+    g = W.ns_grid(args.nx, args.ny)
+    flow = W.shear_bubble_flow(g)
+    k, F = args.k, args.batch
+    stream = torch.cuda.current_stream(dev)
+    op = rr.Operator(g, flow, device=local)
+    phi = op.phi()
+
+    def step(fa, s):
+        shifts, seeds, _ = batch_for(s, rank, world, F, wl.omegas, wl.seed0)
+        fa.refactor(shifts)
+        V, sh, i1 = fa.sketch(k, seeds, phi)
+        U, sig, i2 = fa.modes(V)
+        return sig, sh, i1, i2
+
+    shifts0, _, _ = batch_for(0, rank, world, F, wl.omegas, wl.seed0)
+    fa = rr.Factors(op, shifts0, "fp32", stream)
+    info_last = None
+    for s in range(args.warmup):
+        step(fa, s)
+    torch.cuda.synchronize(dev)
+    barrier(pg, local)
+    torch.cuda.synchronize(dev)
+    _lib.rr_profile_start([args.roofline_class])
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        start.record(stream)
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            sig, sh, i1, i2 = step(fa, args.warmup + s)
+            info_last = (i1, i2)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    launches = _lib.rr_launch_count()
+    cls_ms, cls_n = _lib.rr_profile_read(args.roofline_class)
+    _lib.rr_profile_start([])
+    elapsed_ms = start.elapsed_time(end)
+    barrier(pg, local)
+    elapsed_s = max_over_ranks(pg, elapsed_ms / 1e3, dev)
+    value = F * world * args.steps / elapsed_s
+    clocks = clk.summary()
+
+    # per-class breakdown (one extra profiled step, not part of the value)
+    breakdown = None
+    if args.breakdown:
+        allc = list(_lib.PROFILE_CLASSES)
+        _lib.rr_profile_start(allc)
+        step(fa, 0)
+        torch.cuda.synchronize(dev)
+        breakdown = {c: dict(zip(("ms", "launches"), _lib.rr_profile_read(c))) for c in allc}
+        _lib.rr_profile_start([])
+
+    # roofline of the timed kernel class
+    b, nx = g.b, g.nx
+    hbm, bf16, src = peaks()
+    roof = None
+    if cls_n > 0 and cls_ms > 0:
+        avg_s = cls_ms / 1e3 / cls_n
+        if args.roofline_class == "update":
+            NB = panel_width(8, b)
+            flops = update_flops_per_step(b, nx, NB, F) / (nx * math.ceil(b / NB))
+            ach = flops / avg_s / 1e12
+            roof = {"kernel": "gj_update_kernel<float,32> (trailing rank-32 complex update)",
+                    "bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                    "algorithmic_per_launch": flops, "avg_launch_us": avg_s * 1e6}
+        elif args.roofline_class == "sweep":
+            byts = F * (b * b * 8 + 3 * b * k * 8)
+            ach = byts / avg_s / 1e9
+            roof = {"kernel": "sweep_step_kernel<float> (one streamwise column)",
+                    "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "traffic": None, "peak_source": src,
+                    "algorithmic_per_launch": byts, "avg_launch_us": avg_s * 1e6}
+
+    # FP64 path on a subset of the same frequencies, and sigma error vs it
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        F64 = args.fp64_batch
+        fa.close()
+        shifts, seeds, _ = batch_for(args.warmup, 0, 1, F64, wl.omegas, wl.seed0)
+        f32 = rr.Factors(op, shifts, "fp32", stream)
+        V, sh32, _ = f32.sketch(k, seeds, phi)
+        U, sig32, _ = f32.modes(V)
+        sig32 = sig32.cpu().numpy()
+        sh32 = sh32.cpu().numpy()
+        f32.close()
+        del V, U
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f64 = rr.Factors(op, shifts, "fp64", stream)
+        V, sh64, _ = f64.sketch(k, seeds, phi)
+        U, sig64, _ = f64.modes(V)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t64 = e0.elapsed_time(e1) / 1e3
+        sig64 = sig64.cpu().numpy()
+        sh64 = sh64.cpu().numpy()
+        f64.close()
+        del V, U
+        fp64 = {"value": F64 / t64, "unit": "frequencies/s", "batch": F64,
+                "sigma_rel_err_max": float(np.max(np.abs(sig32 - sig64) / sig64)),
+                "sigma_halko_rel_err_max": float(np.max(np.abs(sh32 - sh64) / sh64)),
+                "note": "one timed batch incl. factor allocation; first FP64 launch"}
+    else:
+        fa.close()
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda *shape, dt: torch.empty(*shape, dtype=dt, pin_memory=True)  # noqa: E731
+        Uh = pin(F, g.n, k, dt=torch.complex128)
+        Vh = pin(F, g.n, k, dt=torch.complex128)
+        Sh = pin(F, k, dt=torch.float64)
+        torch.cuda.synchronize(dev)
+        barrier(pg, local)
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for s in range(args.steps):
+            shifts, seeds, _ = batch_for(args.warmup + s, rank, world, F, wl.omegas, wl.seed0)
+            op2 = rr.Operator(g, flow, device=local)
+            h2d += 3 * g.npts * 8 + F * 16 + F * 8
+            ph = op2.phi()
+            f2 = rr.Factors(op2, shifts, "fp32", stream)
+            V, sh, _ = f2.sketch(k, seeds, ph)
+            U, sig, _ = f2.modes(V)
+            Uh.copy_(U, non_blocking=True)
+            Vh.copy_(V, non_blocking=True)
+            Sh.copy_(sig, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            d2h += Uh.numel() * 16 + Vh.numel() * 16 + Sh.numel() * 8
+            f2.close()
+            op2.close()
+            del U, V, sig, sh
+        wall_e2e = time.perf_counter() - t0
+        wall_e2e = max_over_ranks(pg, wall_e2e, dev)
+        e2e = {"value": F * world * args.steps / wall_e2e, "unit": "frequencies/s",
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        nx_s = 48
+        t = cpu_oracle_sample(g, k, nx_s, float(wl.omegas[0]), 1000)
+        cpu = {"value": 1.0 / (t * g.nx / nx_s), "unit": "frequencies/s",
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one frequency on the first {nx_s} of {g.nx} streamwise columns "
+                         f"(block {g.b}, banded LAPACK LU), time scaled x{g.nx // nx_s}"}
+
+    if rank == 0:
+        line = {
+            "metric": f"resolvent frequencies/sec at N={g.n:,}, k={k} (mixed FP32+FP64 refinement)",
+            "value": value, "unit": "frequencies/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+f64", "data": "synthetic",
+            "config": {"workload": f"ns2d-{g.nx}x{g.ny}-k{k}", "N": g.n, "block": g.b,
+                       "k": k, "frequencies_per_step_per_gpu": F, "omega": "log [0.1,5], 64",
+                       "precision": "fp32 factors/sweeps, fp64 refinement to 1e-10, "
+                                    "fp64 CholeskyQR2 + Jacobi SVD",
+                       "l2": "inputs larger than L2 (factors 4.8 GB per frequency)",
+                       "parallelism": f"frequency shards x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
+            "clocks": clocks, "gpu_launches": launches,
+            "refine": {"iters": max(info_last[0]["refine_iters"], info_last[1]["refine_iters"]),
+                       "residual": max(info_last[0]["refine_residual"],
+                                       info_last[1]["refine_residual"])},
+            "wall_s_timed": wall,
+        }
+        if breakdown:
+            line["breakdown_ms"] = breakdown
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

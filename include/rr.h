@@ -177,6 +177,23 @@ rr_status rr_modes(rr_factors* f, int k, void* V, void* U, double* sigma,
 rr_status rr_gaussian(int nshift, int n, int k, const uint64_t* seeds, const double* phi,
                       void* omega, void* stream);
 
+/* Re-factor an existing factors object for F new shifts (same operator,
+ * count and precision), reusing its device storage: the per-frequency loop of
+ * a frequency sweep without reallocation.  Errors as rr_factor. */
+rr_status rr_refactor(rr_factors* f, const double* shifts);
+
+/* Instrumentation (no counterpart in the paper).  rr_launch_count: kernels
+ * launched by this library in this process since the last rr_profile_start.
+ * rr_profile_start(mask): reset the counters and time every later launch of
+ * the kernel classes whose bit is set in mask with a CUDA event pair on the
+ * launching stream.  Classes: 0 Schur update, 1 pivoted panel, 2 row block,
+ * 3 trailing update, 4 finalize (inverse + X), 5 block sweep step,
+ * 6 FP64 residual, 7 Gram, 8 right multiply, 9 small k x k kernels.
+ * rr_profile_read(cls): summed event time (ms) and launches of a class. */
+long long rr_launch_count(void);
+rr_status rr_profile_start(unsigned mask);
+rr_status rr_profile_read(int cls, double* ms, long long* launches);
+
 /* Number of problems (shifts) and precision of a factors object. */
 rr_status rr_factors_dims(const rr_factors* f, int* nshift, int* prec);
 

@@ -77,7 +77,15 @@ SIGNATURES = {
                        ctypes.POINTER(rr_info)]),
     "rr_modes": (_I, [_P, _I, _P, _P, _P, _I, _D, _I, ctypes.POINTER(rr_info)]),
     "rr_gaussian": (_I, [_I, _I, _I, ctypes.POINTER(ctypes.c_uint64), _P, _P, _P]),
+    "rr_refactor": (_I, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "rr_launch_count": (ctypes.c_longlong, []),
+    "rr_profile_start": (_I, [ctypes.c_uint]),
+    "rr_profile_read": (_I, [_I, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_longlong)]),
 }
+
+PROFILE_CLASSES = {"schur": 0, "panel": 1, "rowblock": 2, "update": 3, "finalize": 4,
+                   "sweep": 5, "residual": 6, "gram": 7, "rightmul": 8, "small": 9}
 
 _lib = None
 
@@ -214,6 +222,28 @@ def rr_modes(h, k, V, U, sigma, orthogonalize=False, refine_tol=1e-10, max_refin
     return st, info
 
 
+def rr_refactor(h, shifts):
+    _check(load().rr_refactor(h, _shift_array(shifts)))
+
+
+def rr_launch_count() -> int:
+    return int(load().rr_launch_count())
+
+
+def rr_profile_start(classes=()):
+    mask = 0
+    for c in classes:
+        mask |= 1 << PROFILE_CLASSES[c]
+    _check(load().rr_profile_start(mask))
+
+
+def rr_profile_read(cls):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(load().rr_profile_read(PROFILE_CLASSES[cls], ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
 def rr_gaussian(seeds, n, k, phi, omega, stream=None):
     sd = np.asarray(seeds, dtype=np.uint64).ravel()
     arr = (ctypes.c_uint64 * sd.size)(*[int(x) for x in sd])
@@ -292,6 +322,13 @@ class Factors:
 
     def _dev(self):
         return f"cuda:{self.op.device}"
+
+    def refactor(self, shifts):
+        s = np.asarray(shifts, dtype=np.complex128).ravel()
+        if s.size != self.F:
+            raise ValueError("refactor needs as many shifts as the factors object holds")
+        rr_refactor(self.handle, s)
+        self.shifts = s
 
     def solve(self, b, adjoint=False, refine_tol=1e-10, max_refine=10, check=True):
         import torch

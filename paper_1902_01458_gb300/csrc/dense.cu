@@ -480,6 +480,7 @@ int grid1d(size_t total, int threads) {
 
 rr_status launch_philox(int F, int N, int k, const uint64_t* seeds, const double* phi,
                         const double* wis, double2* out, cudaStream_t st) {
+  prof_count(1);
   philox_kernel<<<grid1d((size_t)F * N * k, 256), 256, 0, st>>>(F, N, k, seeds, phi, wis, out);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
@@ -487,18 +488,21 @@ rr_status launch_philox(int F, int N, int k, const uint64_t* seeds, const double
 
 rr_status launch_scale_rows(int F, int N, int k, const double* w, double2* x, cudaStream_t st) {
   if (!w) return RR_OK;
+  prof_count(1);
   scale_rows_kernel<<<grid1d((size_t)F * N * k, 256), 256, 0, st>>>(F, N, k, w, x);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }
 
 rr_status launch_convert_d2f(size_t n, const double2* in, float2* out, cudaStream_t st) {
+  prof_count(1);
   d2f_kernel<<<grid1d(n, 256), 256, 0, st>>>(n, in, out);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }
 
 rr_status launch_convert_f2d(size_t n, const float2* in, double2* out, int acc, cudaStream_t st) {
+  prof_count(1);
   f2d_kernel<<<grid1d(n, 256), 256, 0, st>>>(n, in, out, acc);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
@@ -507,7 +511,9 @@ rr_status launch_convert_f2d(size_t n, const float2* in, double2* out, int acc, 
 rr_status launch_colnorm2(int F, int N, int k, const double2* x, double* part, int nblk,
                           double* out, cudaStream_t st) {
   int threads = (256 / k) * k;
+  prof_count(1);
   colnorm2_part_kernel<<<dim3(nblk, F), threads, threads * sizeof(double), st>>>(N, k, nblk, x, part);
+  prof_count(1);
   colnorm2_reduce_kernel<<<(F * k + 127) / 128, 128, 0, st>>>(F, k, nblk, part, out);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
@@ -516,7 +522,10 @@ rr_status launch_colnorm2(int F, int N, int k, const double2* x, double* part, i
 rr_status launch_gram(int F, int N, int k, const double2* Y, double2* part, int nblk, double2* G,
                       cudaStream_t st) {
   size_t smem = (size_t)GRAM_ROWS * k * sizeof(double2);
+  prof_begin(PROF_GRAM, st);
   gram_part_kernel<<<dim3(nblk, F), 256, smem, st>>>(N, k, nblk, Y, part);
+  prof_end(PROF_GRAM, st);
+  prof_count(1);
   gram_reduce_kernel<<<(F * k * k + 127) / 128, 128, 0, st>>>(F, k, nblk, part, G);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
@@ -531,7 +540,9 @@ rr_status launch_cholesky(int F, int k, const double2* G, double2* R, double2* R
                                  96 * 1024));
     attr = true;
   }
+  prof_begin(PROF_SMALL, st);
   cholesky_kernel<<<F, 256, smem, st>>>(k, G, R, Rinv, bad, shift_rel, cond);
+  prof_end(PROF_SMALL, st);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }
@@ -548,13 +559,16 @@ rr_status launch_right_mul(int F, int N, int k, const double2* Y, const double2*
   }
   int nb = (N + RB - 1) / RB;
   if (nb > 152 * 4 / (F > 0 ? F : 1) + 1) nb = 152 * 4 / (F > 0 ? F : 1) + 1;
+  prof_begin(PROF_RIGHTMUL, st);
   right_mul_kernel<<<dim3(nb, F), 256, smem, st>>>(N, k, RB, Y, S, out);
+  prof_end(PROF_RIGHTMUL, st);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }
 
 rr_status launch_small_mul(int F, int k, const double2* A, const double2* B, double2* C,
                            cudaStream_t st) {
+  prof_count(1);
   small_mul_kernel<<<F, 256, 0, st>>>(k, A, B, C);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
@@ -573,13 +587,16 @@ rr_status launch_jacobi_svd(int F, int k, const double2* R, double* sigma, doubl
   }
   int threads = 32 * (kp / 2);
   if (threads < 64) threads = 64;
+  prof_begin(PROF_SMALL, st);
   jacobi_svd_kernel<<<F, threads, smem, st>>>(k, kp, R, sigma, Ul, Vr, sweeps);
+  prof_end(PROF_SMALL, st);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }
 
 rr_status launch_col_scale(int F, int N, int k, const double2* in, const double* sigma,
                            double2* out, cudaStream_t st) {
+  prof_count(1);
   col_scale_kernel<<<grid1d((size_t)F * N * k, 256), 256, 0, st>>>(F, N, k, in, sigma, out);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
@@ -594,11 +611,15 @@ rr_status launch_finish_modes(int F, int N, int k, double2* U, double2* V, doubl
   int threads = (256 / k) * k;
   double* pv = part;
   int* pi = reinterpret_cast<int*>(part + (size_t)F * nblk * k);
+  prof_count(1);
   colmax_part_kernel<<<dim3(nblk, F), threads, threads * (sizeof(double) + sizeof(int)), st>>>(
       N, k, nblk, V, pv, pi);
+  prof_count(1);
   finish_small_kernel<<<F, 64, 0, st>>>(N, k, nblk, pv, pi, V, sigma, rank, phase);
   size_t total = (size_t)F * N * k;
+  prof_count(1);
   permute_phase_kernel<<<grid1d(total, 256), 256, 0, st>>>(F, N, k, rank, phase, U, tmpU);
+  prof_count(1);
   permute_phase_kernel<<<grid1d(total, 256), 256, 0, st>>>(F, N, k, rank, phase, V, tmpV);
   RR_CUDA(cudaMemcpyAsync(U, tmpU, total * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   RR_CUDA(cudaMemcpyAsync(V, tmpV, total * sizeof(double2), cudaMemcpyDeviceToDevice, st));
@@ -615,6 +636,7 @@ __global__ void axpy_kernel(size_t n, const double2* __restrict__ d, double2* __
 }  // namespace
 
 rr_status launch_axpy(size_t n, const double2* d, double2* x, cudaStream_t st) {
+  prof_count(1);
   axpy_kernel<<<grid1d(n, 256), 256, 0, st>>>(n, d, x);
   RR_CUDA(cudaGetLastError());
   return RR_OK;

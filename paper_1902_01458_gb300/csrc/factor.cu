@@ -390,21 +390,32 @@ rr_status factor_impl(rr_factors* fa) {
 
   for (int i = 0; i < nx; ++i) {
     iota_kernel<<<(b * F + 255) / 256, 256, 0, st>>>(fa->perm, b, F);
+    prof_count(1);
     dim3 gs((b + 127) / 128, b, F);
     const C* Xprev = (i > 0) ? X + (size_t)(i - 1) * bb : nullptr;
+    prof_begin(PROF_SCHUR, st);
     schur_kernel<T><<<gs, 128, 0, st>>>(ov, fa->shifts, i, Xprev, xstride, M);
+    prof_end(PROF_SCHUR, st);
     for (int k0 = 0; k0 < b; k0 += NB) {
       const int nbk = std::min(NB, b - k0);
+      prof_begin(PROF_PANEL, st);
       gj_panel_kernel<T, NB><<<F, PANEL_THREADS, psmem, st>>>(b, k0, nbk, M, fa->ipiv,
                                                              fa->perm, fa->flag);
+      prof_end(PROF_PANEL, st);
+      prof_begin(PROF_ROWBLOCK, st);
       gj_rowblock_kernel<T, NB><<<dim3((b + 127) / 128, F), 128, 0, st>>>(b, k0, nbk, M,
                                                                           fa->ipiv, Bbuf);
+      prof_end(PROF_ROWBLOCK, st);
+      prof_begin(PROF_UPDATE, st);
       gj_update_kernel<T, NB><<<dim3((b + 63) / 64, (b + 63) / 64, F), 256, 0, st>>>(
           b, k0, nbk, M, Bbuf);
+      prof_end(PROF_UPDATE, st);
     }
     C* Xi = (i + 1 < nx) ? X + (size_t)i * bb : nullptr;
+    prof_begin(PROF_FINALIZE, st);
     gj_finalize_kernel<T><<<dim3((b + RB - 1) / RB, F), 256, fsmem, st>>>(
         ov, i, RB, M, fa->perm, G + (size_t)i * bb, gstride, Xi, xstride);
+    prof_end(PROF_FINALIZE, st);
     RR_CUDA(cudaGetLastError());
   }
   return RR_OK;

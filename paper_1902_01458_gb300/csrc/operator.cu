@@ -248,6 +248,7 @@ rr_status launch_assemble(OpDev& d, const rr_grid& g, cudaStream_t st) {
   p.re = g.re; p.c2 = (g.kind == RR_ISO_NS2D) ? 1.0 / (g.mach * g.mach) : 0.0;
   p.smax = g.sponge_max; p.sfrac = g.sponge_frac;
   int npts = d.nx * d.ny;
+  prof_count(1);
   assemble_kernel<<<(npts + 127) / 128, 128, 0, st>>>(p, d.flow, d.coef);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
@@ -264,6 +265,7 @@ static int grid_for(size_t total, int threads, int dev) {
 rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
                        const double2* x, double2* y, cudaStream_t st) {
   size_t total = (size_t)F * d.n * k;
+  prof_count(1);
   apply_kernel<false><<<grid_for(total, 256, d.device), 256, 0, st>>>(
       view(d), shifts, F, k, adjoint, nullptr, x, y);
   RR_CUDA(cudaGetLastError());
@@ -273,14 +275,17 @@ rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int 
 rr_status launch_residual(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
                           const double2* b, const double2* x, double2* r, cudaStream_t st) {
   size_t total = (size_t)F * d.n * k;
+  prof_begin(PROF_RESIDUAL, st);
   apply_kernel<true><<<grid_for(total, 256, d.device), 256, 0, st>>>(
       view(d), shifts, F, k, adjoint, b, x, r);
+  prof_end(PROF_RESIDUAL, st);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }
 
 rr_status launch_phi(const OpDev& d, double* phi, cudaStream_t st) {
   int npts = d.nx * d.ny;
+  prof_count(1);
   phi_kernel<<<(npts + 127) / 128, 128, 0, st>>>(d.flow, d.nx, d.ny, d.periodic, d.dx, d.dy,
                                                  d.q, phi);
   RR_CUDA(cudaGetLastError());

@@ -1,0 +1,70 @@
+// Launch counting and optional CUDA-event timing of selected kernel classes.
+// Timing is off unless rr_profile_start enables classes; when on, an event
+// pair brackets every launch of an enabled class on its own stream.
+#include <vector>
+
+#include "rr_internal.cuh"
+
+namespace {
+unsigned g_mask = 0;
+std::vector<cudaEvent_t> g_start[PROF_N], g_stop[PROF_N];
+size_t g_used[PROF_N] = {0};
+long long g_class_launches[PROF_N] = {0};
+long long g_launches = 0;
+}  // namespace
+
+void prof_count(int n) { g_launches += n; }
+
+void prof_begin(int cls, cudaStream_t st) {
+  g_launches += 1;
+  g_class_launches[cls] += 1;
+  if (!(g_mask & (1u << cls))) return;
+  size_t i = g_used[cls];
+  if (i >= g_start[cls].size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+    g_start[cls].push_back(a);
+    g_stop[cls].push_back(b);
+  }
+  cudaEventRecord(g_start[cls][i], st);
+}
+
+void prof_end(int cls, cudaStream_t st) {
+  if (!(g_mask & (1u << cls))) return;
+  size_t i = g_used[cls];
+  if (i >= g_stop[cls].size()) return;
+  cudaEventRecord(g_stop[cls][i], st);
+  g_used[cls] = i + 1;
+}
+
+extern "C" rr_status rr_profile_start(unsigned mask) {
+  g_mask = mask;
+  for (int c = 0; c < PROF_N; ++c) {
+    g_used[c] = 0;
+    g_class_launches[c] = 0;
+  }
+  g_launches = 0;
+  return RR_OK;
+}
+
+extern "C" rr_status rr_profile_read(int cls, double* ms, long long* launches) {
+  if (cls < 0 || cls >= PROF_N) {
+    set_error("rr_profile_read: unknown kernel class");
+    return RR_ERR_ARG;
+  }
+  double total = 0.0;
+  for (size_t i = 0; i < g_used[cls]; ++i) {
+    cudaError_t e = cudaEventSynchronize(g_stop[cls][i]);
+    if (e != cudaSuccess) return cuda_status(e, "rr_profile_read");
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, g_start[cls][i], g_stop[cls][i]);
+    if (e != cudaSuccess) return cuda_status(e, "rr_profile_read");
+    total += t;
+  }
+  if (ms) *ms = total;
+  if (launches) *launches = g_class_launches[cls];
+  return RR_OK;
+}
+
+extern "C" long long rr_launch_count(void) { return g_launches; }

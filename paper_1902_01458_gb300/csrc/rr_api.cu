@@ -616,6 +616,31 @@ extern "C" rr_status rr_modes(rr_factors* fa, int k, void* V, void* U, double* s
   return conv;
 }
 
+extern "C" rr_status rr_refactor(rr_factors* fa, const double* shifts) {
+  if (!fa || !shifts) return arg_error("rr_refactor: null argument");
+  const int F = fa->F;
+  for (int f = 0; f < 2 * F; ++f)
+    if (!std::isfinite(shifts[f])) return arg_error("rr_refactor: shifts must be finite");
+  DeviceGuard guard(fa->op->d.device);
+  cudaStream_t st = fa->stream;
+  // the previous work on the stream may still read shifts_h-derived data
+  RR_CUDA(cudaStreamSynchronize(st));
+  for (int f = 0; f < F; ++f) fa->shifts_h[f] = make_double2(shifts[2 * f], shifts[2 * f + 1]);
+  RR_CUDA(cudaMemcpyAsync(fa->shifts, fa->shifts_h, F * sizeof(double2), cudaMemcpyHostToDevice, st));
+  RR_CUDA(cudaMemsetAsync(fa->flag, 0, F * sizeof(int), st));
+  rr_status s = launch_factor(fa);
+  if (s != RR_OK) return s;
+  std::vector<int> flags(F);
+  RR_CUDA(cudaMemcpyAsync(flags.data(), fa->flag, F * sizeof(int), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  for (int f = 0; f < F; ++f)
+    if (flags[f]) {
+      g_err = "rr_refactor: exact zero pivot";
+      return RR_ERR_SINGULAR;
+    }
+  return RR_OK;
+}
+
 extern "C" rr_status rr_gaussian(int nshift, int n, int k, const uint64_t* seeds, const double* phi,
                                  void* omega, void* stream) {
   if (!seeds || !omega) return arg_error("rr_gaussian: null argument");

@@ -180,4 +180,14 @@ rr_status launch_finish_modes(int F, int N, int k, double2* U, double2* V, doubl
 
 rr_status launch_axpy(size_t n, const double2* d, double2* x, cudaStream_t st);
 
+// prof.cu: launch counting and per-class event timing (classes of rr.h)
+enum {
+  PROF_SCHUR = 0, PROF_PANEL = 1, PROF_ROWBLOCK = 2, PROF_UPDATE = 3, PROF_FINALIZE = 4,
+  PROF_SWEEP = 5, PROF_RESIDUAL = 6, PROF_GRAM = 7, PROF_RIGHTMUL = 8, PROF_SMALL = 9,
+  PROF_OTHER = 10, PROF_N = 11
+};
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st);
+void prof_count(int n);
+
 int num_sms(int device);

@@ -147,8 +147,10 @@ rr_status step(rr_factors* fa, int i, int k, int kp, int RT, const C_t<T>* Mat, 
     attr_set = true;
   }
   dim3 grid((d.b + RT - 1) / RT, fa->F);
+  prof_begin(PROF_SWEEP, fa->stream);
   sweep_step_kernel<T, MODE><<<grid, SW_THREADS, smem, fa->stream>>>(view(d), i, k, kp, RT, Mat,
                                                                     mstride, in, out);
+  prof_end(PROF_SWEEP, fa->stream);
   return RR_OK;
 }
 
