@@ -173,7 +173,7 @@ def update_flops_per_step(b, nx, NB, F):
 def panel_width(prec_bytes, b):
     cap = 227 * 1024 - 2048
     for nb in (32, 16, 8):
-        if b * nb * prec_bytes + 3 * nb * (nb + 1) * prec_bytes <= cap:
+        if b * (nb + 1) * prec_bytes + 3 * nb * (nb + 1) * prec_bytes <= cap:
             return nb
     return 8
 

@@ -99,6 +99,9 @@ typedef struct {
   double refine_residual; /* largest final ||b - A x|| / ||b|| per column  */
   double cqr_cond;        /* largest condition estimate of a CholeskyQR R  */
   int cqr_shifted;        /* 1 if a shifted CholeskyQR fallback was used   */
+  int refine_stagnated;   /* 1 if refinement stopped at the FP64 residual
+                             floor (a correction no longer halved the
+                             residual) above refine_tol                    */
 } rr_info;
 
 const char* rr_last_error(void);

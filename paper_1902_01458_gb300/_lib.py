@@ -48,7 +48,8 @@ class rr_baseflow(ctypes.Structure):
 
 class rr_info(ctypes.Structure):
     _fields_ = [("refine_iters", ctypes.c_int), ("refine_residual", ctypes.c_double),
-                ("cqr_cond", ctypes.c_double), ("cqr_shifted", ctypes.c_int)]
+                ("cqr_cond", ctypes.c_double), ("cqr_shifted", ctypes.c_int),
+                ("refine_stagnated", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

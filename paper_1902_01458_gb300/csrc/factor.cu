@@ -76,7 +76,8 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
                 int* __restrict__ perm_all, int* __restrict__ flag) {
   using C = C_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* P = reinterpret_cast<C*>(smem_raw);  // [b][NB]
+  constexpr int PS = NB + 1;  // padded row stride: column walks hit distinct banks
+  C* P = reinterpret_cast<C*>(smem_raw);  // [b][PS]
   __shared__ C Ui[NB][NB + 1], Li[NB][NB + 1], Ti[NB][NB + 1];
   __shared__ T red_v[PANEL_THREADS / 32];
   __shared__ int red_i[PANEL_THREADS / 32];
@@ -89,7 +90,7 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
 
   for (int e = tid; e < b * nbk; e += nt) {
     int r = e / nbk, c = e - r * nbk;
-    P[r * NB + c] = M[(size_t)r * b + k0 + c];
+    P[r * PS + c] = M[(size_t)r * b + k0 + c];
   }
   __syncthreads();
 
@@ -98,7 +99,7 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
     const int top = k0 + j;
     T bv = (T)-1;
     int bi = b;
-    for (int r = top + tid; r < b; r += nt) amax_merge(bv, bi, cabs2(P[r * NB + j]), r);
+    for (int r = top + tid; r < b; r += nt) amax_merge(bv, bi, cabs2(P[r * PS + j]), r);
     for (int o = 16; o > 0; o >>= 1) {
       T v2 = __shfl_xor_sync(0xffffffffu, bv, o);
       int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -131,20 +132,20 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
     const int p = s_piv;
     if (p != top)
       for (int c = tid; c < nbk; c += nt) {
-        C t = P[top * NB + c];
-        P[top * NB + c] = P[p * NB + c];
-        P[p * NB + c] = t;
+        C t = P[top * PS + c];
+        P[top * PS + c] = P[p * PS + c];
+        P[p * PS + c] = t;
       }
     __syncthreads();
-    C piv = P[top * NB + j];
+    C piv = P[top * PS + j];
     if (cabs2(piv) == (T)0) piv = mk(sizeof(T) == 8 ? (T)1e-150 : (T)1e-18, (T)0);
     const C pinv = cinv(piv);
     for (int r = top + 1 + tid; r < b; r += nt) {
-      C l = cmul(P[r * NB + j], pinv);
-      P[r * NB + j] = l;
+      C l = cmul(P[r * PS + j], pinv);
+      P[r * PS + j] = l;
 #pragma unroll
       for (int c = 0; c < NB; ++c)
-        if (c > j && c < nbk) P[r * NB + c] = csub(P[r * NB + c], cmul(l, P[top * NB + c]));
+        if (c > j && c < nbk) P[r * PS + c] = csub(P[r * PS + c], cmul(l, P[top * PS + c]));
     }
     __syncthreads();
   }
@@ -155,13 +156,13 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
     for (int i = 0; i < NB; ++i) { Ui[i][c] = czero<C>(); Li[i][c] = czero<C>(); }
     for (int i = c; i >= 0; --i) {
       C s = (i == c) ? mk((T)1, (T)0) : czero<C>();
-      for (int m = i + 1; m <= c; ++m) s = csub(s, cmul(P[(k0 + i) * NB + m], Ui[m][c]));
-      Ui[i][c] = cmul(s, cinv(P[(k0 + i) * NB + i]));
+      for (int m = i + 1; m <= c; ++m) s = csub(s, cmul(P[(k0 + i) * PS + m], Ui[m][c]));
+      Ui[i][c] = cmul(s, cinv(P[(k0 + i) * PS + i]));
     }
     Li[c][c] = mk((T)1, (T)0);
     for (int i = c + 1; i < nbk; ++i) {
       C s = czero<C>();
-      for (int m = c; m < i; ++m) s = csub(s, cmul(P[(k0 + i) * NB + m], Li[m][c]));
+      for (int m = c; m < i; ++m) s = csub(s, cmul(P[(k0 + i) * PS + m], Li[m][c]));
       Li[i][c] = s;
     }
   }
@@ -179,12 +180,12 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
     if (r >= k0 && r < k0 + nbk) {
 #pragma unroll
       for (int c = 0; c < NB; ++c)
-        if (c < nbk) P[r * NB + c] = Ti[r - k0][c];
+        if (c < nbk) P[r * PS + c] = Ti[r - k0][c];
       continue;
     }
     C v[NB];
 #pragma unroll
-    for (int m = 0; m < NB; ++m) v[m] = (m < nbk) ? P[r * NB + m] : czero<C>();
+    for (int m = 0; m < NB; ++m) v[m] = (m < nbk) ? P[r * PS + m] : czero<C>();
     const bool above = r < k0;
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
@@ -193,13 +194,13 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
 #pragma unroll
       for (int m = 0; m < NB; ++m)
         if (m < nbk) s = cfma(v[m], above ? Ti[m][c] : Li[m][c], s);
-      P[r * NB + c] = cneg(s);
+      P[r * PS + c] = cneg(s);
     }
   }
   __syncthreads();
   for (int e = tid; e < b * nbk; e += nt) {
     int r = e / nbk, c = e - r * nbk;
-    M[(size_t)r * b + k0 + c] = P[r * NB + c];
+    M[(size_t)r * b + k0 + c] = P[r * PS + c];
   }
 }
 
@@ -360,7 +361,7 @@ int panel_nb(int b) {
   const size_t csz = sizeof(C_t<T>);
   const size_t cap = 227 * 1024 - 2048;
   for (int nb = 32; nb >= 8; nb >>= 1)
-    if ((size_t)b * nb * csz + 3 * (size_t)nb * (nb + 1) * csz <= cap) return nb;
+    if ((size_t)b * (nb + 1) * csz + 3 * (size_t)nb * (nb + 1) * csz <= cap) return nb;
   return 8;
 }
 
@@ -379,7 +380,7 @@ rr_status factor_impl(rr_factors* fa) {
   const size_t gstride = (size_t)nx * bb;          // per problem
   const size_t xstride = (size_t)(nx > 1 ? nx - 1 : 1) * bb;
 
-  const size_t psmem = (size_t)b * NB * sizeof(C);
+  const size_t psmem = (size_t)b * (NB + 1) * sizeof(C);
   RR_CUDA(cudaFuncSetAttribute(gj_panel_kernel<T, NB>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
   int RB = 4;

@@ -172,6 +172,7 @@ void info_reset(rr_info* info) {
   info->refine_residual = 0.0;
   info->cqr_cond = 0.0;
   info->cqr_shifted = 0;
+  info->refine_stagnated = 0;
 }
 
 // x = A^{-1} b (or A^{-H} b) in FP64 [F][N][k], b != x, with FP64 iterative
@@ -199,7 +200,8 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
   std::vector<double> bn((size_t)F * k), rn((size_t)F * k);
   RR_CUDA(cudaMemcpyAsync(bn.data(), w.bn, bn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   int it = 0;
-  double rel = 0.0;
+  double rel = 0.0, prev = INFINITY;
+  int stagnated = 0;
   rr_status result = RR_OK;
   for (;;) {
     if ((s = launch_residual(d, F, fa->shifts, k, adjoint, b, x, w.R64, st)) != RR_OK) return s;
@@ -213,6 +215,14 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
       rel = std::max(rel, r);
     }
     if (tol <= 0.0 || rel <= tol) break;
+    // The FP64 residual itself carries rounding of order u ||A|| ||x||; once a
+    // correction no longer halves the residual, x is as accurate as that
+    // floor allows and further sweeps cannot help.
+    if (it > 0 && rel > 0.5 * prev) {
+      stagnated = 1;
+      break;
+    }
+    prev = rel;
     if (it >= maxit) {
       char buf[160];
       snprintf(buf, sizeof buf, "refinement stopped after %d iterations at relative residual %.3e > %.3e",
@@ -236,6 +246,7 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
   if (info) {
     info->refine_iters = std::max(info->refine_iters, it);
     info->refine_residual = std::max(info->refine_residual, rel);
+    info->refine_stagnated |= stagnated;
   }
   return result;
 }
@@ -448,6 +459,7 @@ extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts
   if ((s = dalloc(&fa->X, (size_t)nshift * std::max(1, d.nx - 1) * bb * fa->csz)) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->M, (size_t)nshift * bb * fa->csz)) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->Bbuf, (size_t)nshift * 32 * d.b * fa->csz)) != RR_OK) return fail(s);
+  if ((s = dalloc(&fa->Tbuf, (size_t)nshift * 64 * d.b * fa->csz)) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->perm, (size_t)nshift * d.b * sizeof(int))) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->ipiv, (size_t)nshift * 32 * sizeof(int))) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->flag, (size_t)nshift * sizeof(int))) != RR_OK) return fail(s);
@@ -485,6 +497,7 @@ extern "C" rr_status rr_destroy_factors(rr_factors* fa) {
   cudaFree(fa->X);
   cudaFree(fa->M);
   cudaFree(fa->Bbuf);
+  cudaFree(fa->Tbuf);
   cudaFree(fa->perm);
   cudaFree(fa->ipiv);
   cudaFree(fa->flag);

@@ -116,6 +116,7 @@ struct rr_factors {
   void* X;           // [F][nx-1][b][b] X_i = G_i C_i
   void* M;           // [F][b][b] work matrix
   void* Bbuf;        // [F][32][b] saved pivot rows of the current panel
+  void* Tbuf;        // [F][b][64] right-hand side block of one sweep step
   int* perm;         // [F][b]
   int* ipiv;         // [F][32]
   int* flag;         // [F] singular-pivot flags
