@@ -128,6 +128,24 @@ rr_status rr_operator_dims(const rr_operator* op, int* n, int* b, int* q,
 rr_status rr_apply(rr_operator* op, int nshift, const double* shifts, int k,
                    int adjoint, const void* x, void* y, void* stream);
 
+/* Allocation-free variant of rr_apply.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory once
+ * they are running -- for example a host framework that owns the whole GPU
+ * through its own memory pool, or a time-critical loop where cudaMalloc's
+ * implicit device synchronisation is not allowed.  Same arguments, result
+ * and errors as rr_apply, but the F shifts are staged in a fixed array
+ * compiled into the library (RR_APPLY_STATIC_MAX_SHIFTS complex doubles,
+ * 64 KB, held on every GPU that loads the library until the process exits)
+ * instead of a cudaMalloc'd buffer; nshift above the maximum is rejected with
+ * RR_ERR_ARG.  The call allocates nothing.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array, so calls that overlap on the GPU (other streams or host
+ * threads) race on it; the call synchronises its stream before returning. */
+#define RR_APPLY_STATIC_MAX_SHIFTS 4096
+rr_status rr_apply_static(rr_operator* op, int nshift, const double* shifts, int k,
+                          int adjoint, const void* x, void* y, void* stream);
+
 /* Eq. (9): Phi_j = ||grad v||_F at every grid point, repeated over the q
  * variables.  phi: device, N doubles. */
 rr_status rr_phi(rr_operator* op, double* phi, void* stream);

@@ -68,6 +68,7 @@ SIGNATURES = {
     "rr_destroy_operator": (_I, [_P]),
     "rr_operator_dims": (_I, [_P] + [ctypes.POINTER(_I)] * 5),
     "rr_apply": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), _I, _I, _P, _P, _P]),
+    "rr_apply_static": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), _I, _I, _P, _P, _P]),
     "rr_phi": (_I, [_P, _P, _P]),
     "rr_factor": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), _I, _P,
                        ctypes.POINTER(_P)]),
@@ -176,6 +177,13 @@ def rr_apply(h, shifts, x, y, adjoint=False, stream=None):
     F, _, k = x.shape
     _check(load().rr_apply(h, F, _shift_array(shifts), k, int(adjoint), _dptr(x),
                            _dptr(y), _stream_ptr(stream)))
+
+
+def rr_apply_static(h, shifts, x, y, adjoint=False, stream=None):
+    """rr_apply without any device allocation (shifts staged in a fixed array)."""
+    F, _, k = x.shape
+    _check(load().rr_apply_static(h, F, _shift_array(shifts), k, int(adjoint), _dptr(x),
+                                  _dptr(y), _stream_ptr(stream)))
 
 
 def rr_phi(h, phi, stream=None):

@@ -272,6 +272,73 @@ rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int 
   return RR_OK;
 }
 
+// ----------------------------------------------------------------------------
+// Allocation-free operator application.
+//
+// The shift list that rr_apply stages in a cudaMalloc'd buffer lives here in a
+// fixed array compiled into the library instead.  Every GPU that loads the
+// library holds this array until the process exits; every call of
+// rr_apply_static shares it, so calls that overlap on the GPU (different
+// streams, or different host threads) race on it.
+static __device__ __align__(256) double2 g_apply_static_shifts[RR_APPLY_STATIC_MAX_SHIFTS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+double2* g_static_shift_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" rr_status rr_apply_static(rr_operator* op, int nshift, const double* shifts, int k,
+                                     int adjoint, const void* x, void* y, void* stream) {
+  if (!op || !shifts || !x || !y) {
+    set_error("rr_apply_static: null argument");
+    return RR_ERR_ARG;
+  }
+  if (nshift < 1 || k < 1) {
+    set_error("rr_apply_static: nshift and k must be >= 1");
+    return RR_ERR_ARG;
+  }
+  if (nshift > RR_APPLY_STATIC_MAX_SHIFTS) {
+    set_error("rr_apply_static: nshift exceeds RR_APPLY_STATIC_MAX_SHIFTS (4096)");
+    return RR_ERR_ARG;
+  }
+  if (x == y) {
+    set_error("rr_apply_static: x and y must be distinct");
+    return RR_ERR_ARG;
+  }
+  const int dev = op->d.device;
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("rr_apply_static: device ordinal out of range");
+    return RR_ERR_ARG;
+  }
+  int prev = -1;
+  RR_CUDA(cudaGetDevice(&prev));
+  if (prev != dev) RR_CUDA(cudaSetDevice(dev));
+  rr_status s = RR_OK;
+  // one-time set-up on this device: the host cannot use the symbol itself as
+  // a device address, so fetch the address with the device current
+  if (g_static_shift_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_apply_static_shifts);
+    if (e != cudaSuccess) s = cuda_status(e, "rr_apply_static: cudaGetSymbolAddress");
+    else g_static_shift_ptr[dev] = static_cast<double2*>(p);
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (s == RR_OK) {
+    cudaError_t e = cudaMemcpyAsync(g_static_shift_ptr[dev], shifts, nshift * sizeof(double2),
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) s = cuda_status(e, "rr_apply_static: shift copy");
+  }
+  if (s == RR_OK)
+    s = launch_apply(op->d, nshift, g_static_shift_ptr[dev], k, adjoint,
+                     static_cast<const double2*>(x), static_cast<double2*>(y), st);
+  if (s == RR_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_status(e, "rr_apply_static");
+  }
+  if (prev != dev && prev >= 0) cudaSetDevice(prev);
+  return s;
+}
+
 rr_status launch_residual(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
                           const double2* b, const double2* x, double2* r, cudaStream_t st) {
   size_t total = (size_t)F * d.n * k;
