@@ -70,19 +70,38 @@ __device__ __forceinline__ void amax_merge(T& v, int& i, T v2, int i2) {
   if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
 }
 
+// Pivoted panel step.  The tall panel M[:, K] sits in shared memory by
+// original row ("slot"); the LU with partial pivoting over slots >= k0 never
+// moves data: each step picks the largest remaining |.|^2 of column j (lowest
+// slot on ties), marks that slot as the j-th pivot and eliminates column j
+// from the other remaining slots, with two block barriers per step (every
+// warp reduces the per-warp candidates itself).  Warp 0 then replays the
+// choices as the equivalent sequence of row interchanges (ipiv, as the row
+// block kernel applies them to the other columns) and the final position of
+// every slot, and the transformed panel is written back in that order:
+//   pivot rows  -> T^{-1} = U11^{-1} L11^{-1}
+//   rows above  -> -row T^{-1}
+//   other rows  -> -(their multipliers) L11^{-1}   (= -M[I,K] T^{-1})
 template <typename T, int NB>
 __global__ void __launch_bounds__(PANEL_THREADS)
 gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restrict__ ipiv_all,
                 int* __restrict__ perm_all, int* __restrict__ flag) {
   using C = C_t<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int PS = NB + 1;  // padded row stride: column walks hit distinct banks
-  C* P = reinterpret_cast<C*>(smem_raw);  // [b][PS]
+  constexpr int NW = PANEL_THREADS / 32;
+  constexpr int MAXOWN = (1024 + PANEL_THREADS - 1) / PANEL_THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* P = reinterpret_cast<C*>(smem_raw);  // [b][PS] by slot
   __shared__ C Ui[NB][NB + 1], Li[NB][NB + 1], Ti[NB][NB + 1];
-  __shared__ T red_v[PANEL_THREADS / 32];
-  __shared__ int red_i[PANEL_THREADS / 32];
-  __shared__ int s_piv;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ T red_v[NW];
+  __shared__ int red_i[NW];
+  __shared__ int chosen[NB];
+  __shared__ int sigK[NB];            // slot that ends at position k0 + j
+  __shared__ int nkPos[32], nkSlot[32];
+  __shared__ int s_nk;
+  __shared__ unsigned touched[32];    // positions outside K that receive another slot
+  const int tid = threadIdx.x, nt = PANEL_THREADS;
+  const int lane = tid & 31, warp = tid >> 5;
   const int f = blockIdx.x;
   C* M = Mall + (size_t)f * b * b;
   int* perm = perm_all + (size_t)f * b;
@@ -92,77 +111,121 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
     int r = e / nbk, c = e - r * nbk;
     P[r * PS + c] = M[(size_t)r * b + k0 + c];
   }
+  if (tid < 32) touched[tid] = 0u;
+  unsigned done = 0u;  // bit t: slot k0 + tid + t*nt already pivoted
   __syncthreads();
 
-  // unblocked right-looking LU with partial pivoting on rows [k0, b)
   for (int j = 0; j < nbk; ++j) {
-    const int top = k0 + j;
     T bv = (T)-1;
     int bi = b;
-    for (int r = top + tid; r < b; r += nt) amax_merge(bv, bi, cabs2(P[r * PS + j]), r);
+#pragma unroll
+    for (int t = 0; t < MAXOWN; ++t) {
+      int r = k0 + tid + t * nt;
+      if (r < b && !(done & (1u << t))) amax_merge(bv, bi, cabs2(P[r * PS + j]), r);
+    }
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       T v2 = __shfl_xor_sync(0xffffffffu, bv, o);
       int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
       amax_merge(bv, bi, v2, i2);
     }
-    if ((tid & 31) == 0) { red_v[tid >> 5] = bv; red_i[tid >> 5] = bi; }
+    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
     __syncthreads();
-    if (tid < 32) {
-      int nw = nt >> 5;
-      bv = tid < nw ? red_v[tid] : (T)-1;
-      bi = tid < nw ? red_i[tid] : b;
-      for (int o = 16; o > 0; o >>= 1) {
-        T v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-        int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-        amax_merge(bv, bi, v2, i2);
-      }
-      if (tid == 0) {
-        if (bi >= b) bi = top;
-        s_piv = bi;
-        ipiv[j] = bi;
-        if (!(bv > (T)0)) flag[f] = 1;
-        if (bi != top) {
-          int t = perm[top];
-          perm[top] = perm[bi];
-          perm[bi] = t;
-        }
-      }
+    bv = lane < NW ? red_v[lane] : (T)-1;
+    bi = lane < NW ? red_i[lane] : b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+      int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      amax_merge(bv, bi, v2, i2);
     }
-    __syncthreads();
-    const int p = s_piv;
-    if (p != top)
-      for (int c = tid; c < nbk; c += nt) {
-        C t = P[top * PS + c];
-        P[top * PS + c] = P[p * PS + c];
-        P[p * PS + c] = t;
-      }
-    __syncthreads();
-    C piv = P[top * PS + j];
+    const int p = bi < b ? bi : k0 + j;  // (bi >= b cannot happen while slots remain)
+    if (tid == 0) {
+      chosen[j] = p;
+      if (!(bv > (T)0)) flag[f] = 1;
+    }
+    C piv = P[p * PS + j];
     if (cabs2(piv) == (T)0) piv = mk(sizeof(T) == 8 ? (T)1e-150 : (T)1e-18, (T)0);
     const C pinv = cinv(piv);
-    for (int r = top + 1 + tid; r < b; r += nt) {
+#pragma unroll
+    for (int t = 0; t < MAXOWN; ++t) {
+      int r = k0 + tid + t * nt;
+      if (r >= b || (done & (1u << t))) continue;
+      if (r == p) { done |= 1u << t; continue; }
       C l = cmul(P[r * PS + j], pinv);
       P[r * PS + j] = l;
 #pragma unroll
       for (int c = 0; c < NB; ++c)
-        if (c > j && c < nbk) P[r * PS + c] = csub(P[r * PS + c], cmul(l, P[top * PS + c]));
+        if (c > j && c < nbk) P[r * PS + c] = csub(P[r * PS + c], cmul(l, P[p * PS + c]));
     }
     __syncthreads();
   }
 
-  // inverses of U11 and of the unit lower L11, then T^{-1} = U11^{-1} L11^{-1}
+  // warp 0: replay the choices as row interchanges (position a = k0 + j with
+  // the current position q of the chosen slot), tracking where slots end
+  if (warp == 0) {
+    int kc = (lane < nbk) ? k0 + lane : -1;  // slot now at position k0 + lane
+    int np = -1, nc = -1, cnt = 0;           // touched position outside K and its slot
+    for (int j = 0; j < nbk; ++j) {
+      const int sj = chosen[j];
+      unsigned bK = __ballot_sync(0xffffffffu, lane < nbk && kc == sj);
+      unsigned bN = __ballot_sync(0xffffffffu, np >= 0 && nc == sj);
+      int q, ql;
+      bool inK;
+      if (bK) {
+        ql = __ffs(bK) - 1;
+        q = k0 + ql;
+        inK = true;
+      } else if (bN) {
+        ql = __ffs(bN) - 1;
+        q = __shfl_sync(0xffffffffu, np, ql);
+        inK = false;
+      } else {
+        ql = cnt++;
+        q = sj;
+        inK = false;
+        if (lane == ql) { np = sj; nc = sj; }
+      }
+      const int ca = __shfl_sync(0xffffffffu, kc, j);
+      const int cq = inK ? __shfl_sync(0xffffffffu, kc, ql) : __shfl_sync(0xffffffffu, nc, ql);
+      if (lane == j) kc = cq;
+      if (inK && lane == ql) kc = ca;
+      if (!inK && lane == ql) nc = ca;
+      if (lane == 0) {
+        ipiv[j] = q;
+        if (q != k0 + j) {
+          int t = perm[k0 + j];
+          perm[k0 + j] = perm[q];
+          perm[q] = t;
+        }
+      }
+      __syncwarp();
+    }
+    if (lane < nbk) sigK[lane] = kc;
+    if (lane < cnt) {
+      nkPos[lane] = np;
+      nkSlot[lane] = nc;
+      atomicOr(&touched[np >> 5], 1u << (np & 31));
+    }
+    if (lane == 0) s_nk = cnt;
+  }
+
+  // inverses of U11 and of the unit lower L11 (rows = chosen slots in order),
+  // then T^{-1} = U11^{-1} L11^{-1}
   if (tid < nbk) {
     const int c = tid;
     for (int i = 0; i < NB; ++i) { Ui[i][c] = czero<C>(); Li[i][c] = czero<C>(); }
     for (int i = c; i >= 0; --i) {
+      const C* row = P + chosen[i] * PS;
       C s = (i == c) ? mk((T)1, (T)0) : czero<C>();
-      for (int m = i + 1; m <= c; ++m) s = csub(s, cmul(P[(k0 + i) * PS + m], Ui[m][c]));
-      Ui[i][c] = cmul(s, cinv(P[(k0 + i) * PS + i]));
+      for (int m = i + 1; m <= c; ++m) s = csub(s, cmul(row[m], Ui[m][c]));
+      Ui[i][c] = cmul(s, cinv(row[i]));
     }
     Li[c][c] = mk((T)1, (T)0);
     for (int i = c + 1; i < nbk; ++i) {
+      const C* row = P + chosen[i] * PS;
       C s = czero<C>();
-      for (int m = c; m < i; ++m) s = csub(s, cmul(P[(k0 + i) * PS + m], Li[m][c]));
+      for (int m = c; m < i; ++m) s = csub(s, cmul(row[m], Li[m][c]));
       Li[i][c] = s;
     }
   }
@@ -175,12 +238,16 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
   }
   __syncthreads();
 
-  // rows: K -> T^{-1};  above -> -row T^{-1};  below (holding L21) -> -row L11^{-1}
+  // transform every slot in place
   for (int r = tid; r < b; r += nt) {
-    if (r >= k0 && r < k0 + nbk) {
+    int jpiv = -1;
+    if (r >= k0)
+      for (int j = 0; j < nbk; ++j)
+        if (chosen[j] == r) jpiv = j;
+    if (jpiv >= 0) {
 #pragma unroll
       for (int c = 0; c < NB; ++c)
-        if (c < nbk) P[r * PS + c] = Ti[r - k0][c];
+        if (c < nbk) P[r * PS + c] = Ti[jpiv][c];
       continue;
     }
     C v[NB];
@@ -198,19 +265,41 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
     }
   }
   __syncthreads();
+  // write back by position: K positions take their pivot slot, touched
+  // positions outside K take the displaced slot, the rest keep their own
+  const int nk = s_nk;
   for (int e = tid; e < b * nbk; e += nt) {
-    int r = e / nbk, c = e - r * nbk;
-    M[(size_t)r * b + k0 + c] = P[r * PS + c];
+    int a = e / nbk, c = e - a * nbk;
+    int slot = a;
+    if (a >= k0 && a < k0 + nbk) {
+      slot = sigK[a - k0];
+    } else if (touched[a >> 5] & (1u << (a & 31))) {
+      for (int t = 0; t < nk; ++t)
+        if (nkPos[t] == a) slot = nkSlot[t];
+    }
+    M[(size_t)a * b + k0 + c] = P[slot * PS + c];
   }
 }
 
 // Row swaps + B save + M[K,R] <- T^{-1} B for the columns outside the panel.
+// Warp 0 first turns the panel's sequence of swaps into the net movement of
+// at most 2*NB rows; every thread then moves its column with independent
+// loads (all issued before any store) instead of a chain of dependent swaps.
 template <typename T, int NB>
-__global__ void gj_rowblock_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall,
-                                   const int* __restrict__ ipiv_all, C_t<T>* __restrict__ Ball) {
+__host__ __device__ constexpr int rb_threads() {
+  return (NB * 128 * (int)sizeof(C_t<T>) > 32768) ? 32768 / (NB * (int)sizeof(C_t<T>)) : 128;
+}
+template <typename T, int NB>
+__global__ void __launch_bounds__(128)
+gj_rowblock_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall,
+                   const int* __restrict__ ipiv_all, C_t<T>* __restrict__ Ball) {
   using C = C_t<T>;
   __shared__ C Ts[NB][NB + 1];
-  __shared__ int piv[NB];
+  __shared__ int srcK[NB];       // original row now at position k0 + j
+  __shared__ int nkPos[32], nkSrc[32];
+  __shared__ int s_nk;
+  constexpr int RBT = rb_threads<T, NB>();
+  __shared__ C W[NB][RBT];        // values moving to positions outside K
   const int f = blockIdx.y;
   C* M = Mall + (size_t)f * b * b;
   C* B = Ball + (size_t)f * NB * b;
@@ -218,24 +307,55 @@ __global__ void gj_rowblock_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ 
     int i = e / nbk, c = e - i * nbk;
     Ts[i][c] = M[(size_t)(k0 + i) * b + k0 + c];
   }
-  if (threadIdx.x < nbk) piv[threadIdx.x] = ipiv_all[f * 32 + threadIdx.x];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int j = lane; j < NB; j += 32) srcK[j] = k0 + j;
+    int myPos = -1, myCont = -1, nk = 0;
+    __syncwarp();
+    for (int j = 0; j < nbk; ++j) {
+      const int a = k0 + j;
+      const int p = ipiv_all[f * 32 + j];
+      if (p == a) continue;
+      if (p < k0 + nbk) {
+        if (lane == 0) {
+          int t = srcK[j];
+          srcK[j] = srcK[p - k0];
+          srcK[p - k0] = t;
+        }
+        __syncwarp();
+        continue;
+      }
+      unsigned hit = __ballot_sync(0xffffffffu, myPos == p);
+      int owner;
+      if (hit) {
+        owner = __ffs(hit) - 1;
+      } else {
+        owner = nk;
+        if (lane == owner) { myPos = p; myCont = p; }
+        ++nk;
+      }
+      int kc = srcK[j];
+      int oc = __shfl_sync(0xffffffffu, myCont, owner);
+      if (lane == owner) myCont = kc;
+      __syncwarp();
+      if (lane == 0) srcK[j] = oc;
+      __syncwarp();
+    }
+    if (lane < nk) { nkPos[lane] = myPos; nkSrc[lane] = myCont; }
+    if (lane == 0) s_nk = nk;
+  }
   __syncthreads();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= b || (c >= k0 && c < k0 + nbk)) return;
-  for (int j = 0; j < nbk; ++j) {
-    int p = piv[j];
-    if (p != k0 + j) {
-      C t = M[(size_t)(k0 + j) * b + c];
-      M[(size_t)(k0 + j) * b + c] = M[(size_t)p * b + c];
-      M[(size_t)p * b + c] = t;
-    }
-  }
+  const int nk = s_nk;
   C v[NB];
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    v[j] = (j < nbk) ? M[(size_t)(k0 + j) * b + c] : czero<C>();
+  for (int j = 0; j < NB; ++j) v[j] = (j < nbk) ? M[(size_t)srcK[j] * b + c] : czero<C>();
+  for (int t = 0; t < nk; ++t) W[t][threadIdx.x] = M[(size_t)nkSrc[t] * b + c];
+  for (int t = 0; t < nk; ++t) M[(size_t)nkPos[t] * b + c] = W[t][threadIdx.x];
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
     if (j < nbk) B[(size_t)j * b + c] = v[j];
-  }
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     if (i >= nbk) continue;
@@ -247,17 +367,19 @@ __global__ void gj_rowblock_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ 
   }
 }
 
-// Trailing update M[I,R] += M[I,K] B on 64 x 64 tiles (16 x 16 threads, 4 x 4 each).
+// Trailing update M[I,R] += M[I,K] B on 64 x 64 tiles (16 x 16 threads, 4 x 4
+// each) for the columns [c_begin, c_end) outside K and outside [ex_lo, ex_hi).
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
-gj_update_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, const C_t<T>* __restrict__ Ball) {
+gj_update_kernel(int b, int k0, int nbk, int c_begin, int c_end, int ex_lo, int ex_hi,
+                 C_t<T>* __restrict__ Mall, const C_t<T>* __restrict__ Ball) {
   using C = C_t<T>;
   __shared__ C As[64][NB + 1];
   __shared__ C Bs[NB][64];
   const int f = blockIdx.z;
   C* M = Mall + (size_t)f * b * b;
   const C* B = Ball + (size_t)f * NB * b;
-  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const int r0 = blockIdx.y * 64, c0 = c_begin + blockIdx.x * 64;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int e = tid; e < 64 * NB; e += 256) {
     int rr = e / NB, m = e - rr * NB;
@@ -267,7 +389,7 @@ gj_update_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, const C_t<T>
   for (int e = tid; e < NB * 64; e += 256) {
     int m = e / 64, cc = e - m * 64;
     int c = c0 + cc;
-    Bs[m][cc] = (c < b && m < nbk) ? B[(size_t)m * b + c] : czero<C>();
+    Bs[m][cc] = (c < c_end && m < nbk) ? B[(size_t)m * b + c] : czero<C>();
   }
   __syncthreads();
   C acc[4][4];
@@ -294,7 +416,7 @@ gj_update_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, const C_t<T>
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
       int c = c0 + tx + 16 * d;
-      if (c >= b || (c >= k0 && c < k0 + nbk)) continue;
+      if (c >= c_end || (c >= k0 && c < k0 + nbk) || (c >= ex_lo && c < ex_hi)) continue;
       size_t o = (size_t)r * b + c;
       M[o] = cadd(M[o], acc[a][d]);
     }
@@ -360,7 +482,8 @@ template <typename T>
 int panel_nb(int b) {
   const size_t csz = sizeof(C_t<T>);
   const size_t cap = 227 * 1024 - 2048;
-  for (int nb = 32; nb >= 8; nb >>= 1)
+  // complex double keeps NB <= 16 so the static NB x NB scratch stays small
+  for (int nb = (csz == 16 ? 16 : 32); nb >= 8; nb >>= 1)
     if ((size_t)b * (nb + 1) * csz + 3 * (size_t)nb * (nb + 1) * csz <= cap) return nb;
   return 8;
 }
@@ -378,7 +501,7 @@ rr_status factor_impl(rr_factors* fa) {
   C* Bbuf = reinterpret_cast<C*>(fa->Bbuf);
   const size_t bb = (size_t)b * b;
   const size_t gstride = (size_t)nx * bb;          // per problem
-  const size_t xstride = (size_t)(nx > 1 ? nx - 1 : 1) * bb;
+  const size_t xstride = bb;  // X_i is transient: one b x b block per problem
 
   const size_t psmem = (size_t)b * (NB + 1) * sizeof(C);
   RR_CUDA(cudaFuncSetAttribute(gj_panel_kernel<T, NB>,
@@ -389,30 +512,55 @@ rr_status factor_impl(rr_factors* fa) {
   RR_CUDA(cudaFuncSetAttribute(gj_finalize_kernel<T>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
 
+  // look-ahead: panel p+1 runs on a second stream while the trailing update
+  // of panel p proceeds on the main stream (disjoint columns of M)
+  cudaStream_t st2 = fa->stream2;
+  const int P = (b + NB - 1) / NB;
+  auto update = [&](int k0, int nbk, int cb, int ce, int exl, int exh) {
+    const int ntile = (ce - cb + 63) / 64;
+    prof_begin(PROF_UPDATE, st);
+    gj_update_kernel<T, NB><<<dim3(ntile, (b + 63) / 64, F), 256, 0, st>>>(
+        b, k0, nbk, cb, ce, exl, exh, M, Bbuf);
+    prof_end(PROF_UPDATE, st);
+  };
+  auto panel = [&](int p, cudaStream_t s) {
+    const int k0 = p * NB, nbk = std::min(NB, b - k0);
+    prof_begin(PROF_PANEL, s);
+    gj_panel_kernel<T, NB><<<F, PANEL_THREADS, psmem, s>>>(b, k0, nbk, M, fa->ipiv, fa->perm,
+                                                          fa->flag);
+    prof_end(PROF_PANEL, s);
+  };
   for (int i = 0; i < nx; ++i) {
     iota_kernel<<<(b * F + 255) / 256, 256, 0, st>>>(fa->perm, b, F);
     prof_count(1);
     dim3 gs((b + 127) / 128, b, F);
-    const C* Xprev = (i > 0) ? X + (size_t)(i - 1) * bb : nullptr;
+    const C* Xprev = (i > 0) ? X : nullptr;
     prof_begin(PROF_SCHUR, st);
     schur_kernel<T><<<gs, 128, 0, st>>>(ov, fa->shifts, i, Xprev, xstride, M);
     prof_end(PROF_SCHUR, st);
-    for (int k0 = 0; k0 < b; k0 += NB) {
-      const int nbk = std::min(NB, b - k0);
-      prof_begin(PROF_PANEL, st);
-      gj_panel_kernel<T, NB><<<F, PANEL_THREADS, psmem, st>>>(b, k0, nbk, M, fa->ipiv,
-                                                             fa->perm, fa->flag);
-      prof_end(PROF_PANEL, st);
+    panel(0, st);
+    for (int p = 0; p < P; ++p) {
+      const int k0 = p * NB, nbk = std::min(NB, b - k0);
       prof_begin(PROF_ROWBLOCK, st);
-      gj_rowblock_kernel<T, NB><<<dim3((b + 127) / 128, F), 128, 0, st>>>(b, k0, nbk, M,
-                                                                          fa->ipiv, Bbuf);
+      constexpr int RBT = rb_threads<T, NB>();
+      gj_rowblock_kernel<T, NB><<<dim3((b + RBT - 1) / RBT, F), RBT, 0, st>>>(
+          b, k0, nbk, M, fa->ipiv, Bbuf);
       prof_end(PROF_ROWBLOCK, st);
-      prof_begin(PROF_UPDATE, st);
-      gj_update_kernel<T, NB><<<dim3((b + 63) / 64, (b + 63) / 64, F), 256, 0, st>>>(
-          b, k0, nbk, M, Bbuf);
-      prof_end(PROF_UPDATE, st);
+      if (p + 1 < P && st2 != nullptr) {
+        const int n0 = k0 + nbk, n1 = std::min(b, n0 + NB);
+        update(k0, nbk, n0, n1, 0, 0);
+        RR_CUDA(cudaEventRecord(fa->ev_next, st));
+        RR_CUDA(cudaStreamWaitEvent(st2, fa->ev_next, 0));
+        panel(p + 1, st2);
+        RR_CUDA(cudaEventRecord(fa->ev_panel, st2));
+        update(k0, nbk, 0, b, n0, n1);
+        RR_CUDA(cudaStreamWaitEvent(st, fa->ev_panel, 0));
+      } else {
+        update(k0, nbk, 0, b, 0, 0);
+        if (p + 1 < P) panel(p + 1, st);
+      }
     }
-    C* Xi = (i + 1 < nx) ? X + (size_t)i * bb : nullptr;
+    C* Xi = (i + 1 < nx) ? X : nullptr;
     prof_begin(PROF_FINALIZE, st);
     gj_finalize_kernel<T><<<dim3((b + RB - 1) / RB, F), 256, fsmem, st>>>(
         ov, i, RB, M, fa->perm, G + (size_t)i * bb, gstride, Xi, xstride);

@@ -456,14 +456,24 @@ extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts
     return st;
   };
   if ((s = dalloc(&fa->G, (size_t)nshift * d.nx * bb * fa->csz)) != RR_OK) return fail(s);
-  if ((s = dalloc(&fa->X, (size_t)nshift * std::max(1, d.nx - 1) * bb * fa->csz)) != RR_OK) return fail(s);
+  if ((s = dalloc(&fa->X, (size_t)nshift * bb * fa->csz)) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->M, (size_t)nshift * bb * fa->csz)) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->Bbuf, (size_t)nshift * 32 * d.b * fa->csz)) != RR_OK) return fail(s);
-  if ((s = dalloc(&fa->Tbuf, (size_t)nshift * 64 * d.b * fa->csz)) != RR_OK) return fail(s);
+  if ((s = dalloc(&fa->Tbuf, (size_t)nshift * 128 * d.b * fa->csz)) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->perm, (size_t)nshift * d.b * sizeof(int))) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->ipiv, (size_t)nshift * 32 * sizeof(int))) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->flag, (size_t)nshift * sizeof(int))) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->shifts, (size_t)nshift * sizeof(double2))) != RR_OK) return fail(s);
+  {
+    // the look-ahead panel stream gets the highest priority so its CTAs are
+    // scheduled ahead of the trailing update's as SMs free up
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    cudaError_t e1 = cudaStreamCreateWithPriority(&fa->stream2, cudaStreamNonBlocking, hi_prio);
+    if (e1 == cudaSuccess) e1 = cudaEventCreateWithFlags(&fa->ev_next, cudaEventDisableTiming);
+    if (e1 == cudaSuccess) e1 = cudaEventCreateWithFlags(&fa->ev_panel, cudaEventDisableTiming);
+    if (e1 != cudaSuccess) return fail(cuda_status(e1, "rr_factor: stream/event creation"));
+  }
   fa->shifts_h = new double2[nshift];
   for (int f = 0; f < nshift; ++f) fa->shifts_h[f] = make_double2(shifts[2 * f], shifts[2 * f + 1]);
   cudaStream_t st = fa->stream;
@@ -503,6 +513,12 @@ extern "C" rr_status rr_destroy_factors(rr_factors* fa) {
   cudaFree(fa->flag);
   cudaFree(fa->shifts);
   cudaFree(fa->ws);
+  if (fa->stream2) {
+    cudaStreamSynchronize(fa->stream2);
+    cudaStreamDestroy(fa->stream2);
+  }
+  if (fa->ev_next) cudaEventDestroy(fa->ev_next);
+  if (fa->ev_panel) cudaEventDestroy(fa->ev_panel);
   delete[] fa->shifts_h;
   delete fa;
   return RR_OK;

@@ -111,12 +111,14 @@ struct rr_factors {
   int F;
   int prec;          // rr_precision
   cudaStream_t stream;
+  cudaStream_t stream2;  // look-ahead panel stream (owned)
+  cudaEvent_t ev_next, ev_panel;
   size_t csz;        // bytes of one complex element of the factors
   void* G;           // [F][nx][b][b]   inverse of each Schur block
-  void* X;           // [F][nx-1][b][b] X_i = G_i C_i
+  void* X;           // [F][b][b] X_i = G_i C_i of the current column (transient)
   void* M;           // [F][b][b] work matrix
   void* Bbuf;        // [F][32][b] saved pivot rows of the current panel
-  void* Tbuf;        // [F][b][64] right-hand side block of one sweep step
+  void* Tbuf;        // [2][F][b][64] staging blocks of one sweep step
   int* perm;         // [F][b]
   int* ipiv;         // [F][32]
   int* flag;         // [F] singular-pivot flags

@@ -87,6 +87,7 @@ def test_gaussian_matches_oracle(env):
 SOLVE_CASES = [
     ("ns-24x20", lambda: W.config_small_ns(24, 20).grid, None),
     ("ns-random-11x14", lambda: W.ns_grid(11, 14), "random"),
+    ("ns-9x40-four-panels", lambda: W.ns_grid(9, 40), "random"),
     ("advdiff-periodic", lambda: W.Grid(kind=W.KIND_ADVDIFF, nx=9, ny=12, x0=0, x1=2,
                                         y0=0, y1=3, re=5.0, periodic_y=True), "vconst"),
 ]
