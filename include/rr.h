@@ -53,11 +53,14 @@ typedef enum {
 } rr_status;
 
 /* Arithmetic of the block factorisation and the block sweeps.  FP64 runs
- * everything in complex double.  FP32 stores the factors and runs the
- * sweeps in complex float and wins accuracy back by iterative refinement
- * against an FP64 residual; QR, SVD, norms and the refinement residual stay
- * FP64 in every mode. */
-typedef enum { RR_FP64 = 0, RR_FP32 = 1 } rr_precision;
+ * everything in complex double.  FP32 stores the factors in complex float,
+ * runs the sweep products on the tensor cores (tcgen05 kind::tf32 with each
+ * operand split into a TF32 part and its remainder: FP32-level products,
+ * FP32 accumulation) and wins accuracy back by iterative refinement against
+ * an FP64 residual.  FP32_SIMT is the same with every product on the FP32
+ * CUDA cores.  QR, SVD, norms and the refinement residual stay FP64 in every
+ * mode. */
+typedef enum { RR_FP64 = 0, RR_FP32 = 1, RR_FP32_SIMT = 2 } rr_precision;
 
 /* Operator kinds (q = unknowns per grid point). */
 enum { RR_ADVDIFF_SCALAR = 1, RR_ISO_NS2D = 3 };

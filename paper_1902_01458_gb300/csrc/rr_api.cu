@@ -2,6 +2,8 @@
 // Algorithm 1 (Sec. II.B) over the device kernels.  Every step of the path
 // runs on the GPU; the host only sequences launches and, for the iterative
 // refinement of the FP32 factors, reads back residual norms.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -207,7 +209,13 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
     if ((s = launch_residual(d, F, fa->shifts, k, adjoint, b, x, w.R64, st)) != RR_OK) return s;
     if ((s = launch_colnorm2(F, d.n, k, w.R64, w.dpart, w.nblk_col, w.rn, st)) != RR_OK) return s;
     RR_CUDA(cudaMemcpyAsync(rn.data(), w.rn, rn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int tc_err = 0;
+    RR_CUDA(cudaMemcpyAsync(&tc_err, fa->flag + F, sizeof(int), cudaMemcpyDeviceToHost, st));
     RR_CUDA(cudaStreamSynchronize(st));
+    if (tc_err) {
+      g_err = "a tensor-core sweep kernel timed out waiting for its MMAs";
+      return RR_ERR_TIMEOUT;
+    }
     rel = 0.0;
     for (size_t e = 0; e < rn.size(); ++e) {
       double r = bn[e] > 0.0 ? rn[e] / bn[e] : rn[e];
@@ -304,6 +312,39 @@ rr_status cholqr2(rr_factors* fa, int k, double2* Y, double2* Rout, Work& w, rr_
 }
 
 }  // namespace
+
+// TMA tensor maps over all FP32 factors G [F][nx][b][b] (complex, viewed as
+// floats [F*nx][b][2b]): tiles of 128 rows x 32 complex (G) and of 32 rows x
+// 128 complex (for G^H).  Used only when b >= 128 and the row pitch is a
+// multiple of 16 bytes (b even); otherwise the sweeps use cp.async kernels.
+static int encode_factor_maps(rr_factors* fa) {
+  const OpDev& d = fa->op->d;
+  if (d.b < 128 || (d.b & 1)) return 0;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || fn == nullptr) {
+      cudaGetLastError();
+      return 0;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * d.b, (cuuint64_t)d.b, (cuuint64_t)fa->F * d.nx};
+  const cuuint64_t strides[2] = {(cuuint64_t)2 * d.b * 4, (cuuint64_t)2 * d.b * d.b * 4};
+  const cuuint32_t boxN[3] = {64, 128, 1}, boxT[3] = {256, 32, 1}, es[3] = {1, 1, 1};
+  CUresult r1 = encode(reinterpret_cast<CUtensorMap*>(fa->tmap[0]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                       3, fa->G, dims, strides, boxN, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = encode(reinterpret_cast<CUtensorMap*>(fa->tmap[1]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                       3, fa->G, dims, strides, boxT, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? 1 : 0;
+}
 
 // ----------------------------------------------------------------- operator
 extern "C" rr_status rr_create_operator(const rr_grid* g, const rr_baseflow* fl,
@@ -437,7 +478,8 @@ extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts
   if (!op || !shifts || !out) return arg_error("rr_factor: null argument");
   *out = nullptr;
   if (nshift < 1 || nshift > 65535) return arg_error("rr_factor: nshift must be in [1, 65535]");
-  if (prec != RR_FP64 && prec != RR_FP32) return arg_error("rr_factor: unknown precision");
+  if (prec != RR_FP64 && prec != RR_FP32 && prec != RR_FP32_SIMT)
+    return arg_error("rr_factor: unknown precision");
   for (int f = 0; f < 2 * nshift; ++f)
     if (!std::isfinite(shifts[f])) return arg_error("rr_factor: shifts must be finite");
   DeviceGuard guard(op->d.device);
@@ -460,9 +502,15 @@ extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts
   if ((s = dalloc(&fa->M, (size_t)nshift * bb * fa->csz)) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->Bbuf, (size_t)nshift * 32 * d.b * fa->csz)) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->Tbuf, (size_t)nshift * 128 * d.b * fa->csz)) != RR_OK) return fail(s);
+  if (prec == RR_FP32) {
+    if ((s = dalloc(&fa->Pbuf, (size_t)4 * nshift * 64 * d.b * sizeof(float2))) != RR_OK)
+      return fail(s);
+    fa->tma_ok = encode_factor_maps(fa);
+  }
   if ((s = dalloc(&fa->perm, (size_t)nshift * d.b * sizeof(int))) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->ipiv, (size_t)nshift * 32 * sizeof(int))) != RR_OK) return fail(s);
-  if ((s = dalloc(&fa->flag, (size_t)nshift * sizeof(int))) != RR_OK) return fail(s);
+  // flags: one singular-pivot flag per shift, then the tensor-core wait flag
+  if ((s = dalloc(&fa->flag, (size_t)(nshift + 1) * sizeof(int))) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->shifts, (size_t)nshift * sizeof(double2))) != RR_OK) return fail(s);
   {
     // the look-ahead panel stream gets the highest priority so its CTAs are
@@ -480,7 +528,7 @@ extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts
   cudaError_t e = cudaMemcpyAsync(fa->shifts, fa->shifts_h, nshift * sizeof(double2),
                                   cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return fail(cuda_status(e, "rr_factor shifts"));
-  e = cudaMemsetAsync(fa->flag, 0, nshift * sizeof(int), st);
+  e = cudaMemsetAsync(fa->flag, 0, (nshift + 1) * sizeof(int), st);
   if (e != cudaSuccess) return fail(cuda_status(e, "rr_factor flags"));
   if ((s = launch_factor(fa)) != RR_OK) return fail(s);
   std::vector<int> flags(nshift);
@@ -508,6 +556,7 @@ extern "C" rr_status rr_destroy_factors(rr_factors* fa) {
   cudaFree(fa->M);
   cudaFree(fa->Bbuf);
   cudaFree(fa->Tbuf);
+  cudaFree(fa->Pbuf);
   cudaFree(fa->perm);
   cudaFree(fa->ipiv);
   cudaFree(fa->flag);
@@ -656,7 +705,7 @@ extern "C" rr_status rr_refactor(rr_factors* fa, const double* shifts) {
   RR_CUDA(cudaStreamSynchronize(st));
   for (int f = 0; f < F; ++f) fa->shifts_h[f] = make_double2(shifts[2 * f], shifts[2 * f + 1]);
   RR_CUDA(cudaMemcpyAsync(fa->shifts, fa->shifts_h, F * sizeof(double2), cudaMemcpyHostToDevice, st));
-  RR_CUDA(cudaMemsetAsync(fa->flag, 0, F * sizeof(int), st));
+  RR_CUDA(cudaMemsetAsync(fa->flag, 0, (F + 1) * sizeof(int), st));
   rr_status s = launch_factor(fa);
   if (s != RR_OK) return s;
   std::vector<int> flags(F);

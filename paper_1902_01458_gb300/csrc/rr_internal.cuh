@@ -119,6 +119,9 @@ struct rr_factors {
   void* M;           // [F][b][b] work matrix
   void* Bbuf;        // [F][32][b] saved pivot rows of the current panel
   void* Tbuf;        // [2][F][b][64] staging blocks of one sweep step
+  void* Pbuf;        // [4][F][b][64] partial products of the split tensor-core sweep
+  alignas(64) unsigned char tmap[2][128];  // TMA maps of G and of G^H tiles (FP32)
+  int tma_ok;        // 1 if the tensor maps were encoded
   int* perm;         // [F][b]
   int* ipiv;         // [F][32]
   int* flag;         // [F] singular-pivot flags

@@ -14,8 +14,12 @@
 // into a b x k staging block before (or after) it.  One launch per streamwise
 // column covers all F problems of the batch.
 #include <algorithm>
+#include <type_traits>
+
+#include <cuda.h>
 
 #include "rr_internal.cuh"
+#include "tc.cuh"
 
 namespace {
 
@@ -236,12 +240,419 @@ sweep_step_kernel(int b, int k, int kp, int RT, size_t NK, int ob,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core sweep step (complex FP32 factors, tcgen05 kind::tf32).
+//
+// The complex product acc = op(G) t (128 rows of G per CTA, all k columns)
+// is one real GEMM: the interleaved rows of op(G) are the K-major A operand
+// (K = 2 * 32 reals per chunk) and the right-hand side chunk is expanded to
+// the 2k x 64 real matrix Bt with rows (Re t, -Im t, ...) and (Im t, Re t, ...),
+// so D = A Bt^T holds (Re, Im) pairs of the complex result.  FP32 accuracy
+// comes from splitting every operand into a round-to-nearest TF32 part and
+// its remainder, A Bt ~ Ahi Bhi + Ahi Blo + Alo Bhi (3 MMAs per K step).
+// Raw tiles arrive by cp.async (double-buffered); one thread issues the MMAs
+// into a TMEM accumulator and commits them to an mbarrier; warps 0-3 read the
+// 128 x 2k accumulator back with tcgen05.ld.  Waits are bounded: on timeout
+// the kernel sets *err, drains its copies, frees TMEM and returns.
+constexpr int TC_RT = 128, TC_KC = 32, TC_THREADS = 256;
+constexpr uint32_t TC_LBO = 128, TC_SBO = 2048;   // 64 reals of K per 8-row group
+constexpr uint32_t TC_WAIT_TRIES = 1u << 22;
+
+__host__ __device__ constexpr size_t tc_smem_bytes(int kp, bool trans) {
+  return 2 * 32768 + 2 * (size_t)(2 * kp / 8) * TC_SBO +
+         2 * (size_t)((trans ? TC_KC * (TC_RT + 1) : TC_RT * (TC_KC + 1)) + TC_KC * kp) * 8;
+}
+
+template <bool TRANS, int EPI>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+sweep_tc_kernel(int b, int k, int kp, size_t NK, int ob, const float2* __restrict__ Mat,
+                size_t mstride, const float2* rhs, size_t rstride, float2* out, float2* tmp,
+                size_t tstride, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_ok;
+  const int N = 2 * kp;
+  const uint32_t bt_bytes = (uint32_t)(N / 8) * TC_SBO;
+  // operand tiles start on a 1 KB boundary (the launch adds 1 KB of slack)
+  unsigned char* A_hi = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  unsigned char* A_lo = A_hi + 32768;
+  unsigned char* B_hi = A_lo + 32768;
+  unsigned char* B_lo = B_hi + bt_bytes;
+  float2* raw = reinterpret_cast<float2*>(B_lo + bt_bytes);
+  const int raw_ms = TRANS ? TC_KC * (TC_RT + 1) : TC_RT * (TC_KC + 1);
+  const int raw_elems = raw_ms + TC_KC * kp;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int f = blockIdx.y;
+  const int r0 = blockIdx.x * TC_RT;
+  const float2* Mf = Mat + (size_t)f * mstride;
+  const float2* rf = rhs + (size_t)f * rstride;
+  const uint32_t ncols = N <= 32 ? 32u : (N <= 64 ? 64u : 128u);
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, ncols);
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    s_ok = 1;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  auto load_raw = [&](int stage, int m0) {
+    float2* Ms = raw + stage * raw_elems;
+    float2* Ts = Ms + raw_ms;
+    if (!TRANS) {
+      for (int e = tid; e < TC_RT * TC_KC; e += TC_THREADS) {
+        int rr = e / TC_KC, mm = e - rr * TC_KC;
+        int r = r0 + rr, m = m0 + mm;
+        bool ok = r < b && m < b;
+        cp_async_elem(&Ms[rr * (TC_KC + 1) + mm], ok ? Mf + (size_t)r * b + m : Mf, ok);
+      }
+    } else {
+      for (int e = tid; e < TC_RT * TC_KC; e += TC_THREADS) {
+        int mm = e / TC_RT, rr = e - mm * TC_RT;
+        int r = r0 + rr, m = m0 + mm;
+        bool ok = r < b && m < b;
+        cp_async_elem(&Ms[mm * (TC_RT + 1) + rr], ok ? Mf + (size_t)m * b + r : Mf, ok);
+      }
+    }
+    for (int e = tid; e < TC_KC * kp; e += TC_THREADS) {
+      int mm = e / kp, j = e - mm * kp;
+      int m = m0 + mm;
+      bool ok = m < b && j < k;
+      cp_async_elem(&Ts[mm * kp + j], ok ? rf + (size_t)m * k + j : rf, ok);
+    }
+  };
+
+  const int nch = (b + TC_KC - 1) / TC_KC;
+  const uint32_t idesc = tc::idesc_tf32(TC_RT, N);
+  load_raw(0, 0);
+  cp_async_commit();
+  for (int c = 0; c < nch; ++c) {
+    cp_async_wait<0>();
+    __syncthreads();
+    if (c + 1 < nch) load_raw((c + 1) & 1, (c + 1) * TC_KC);
+    cp_async_commit();
+    if (c > 0) {  // the MMAs of chunk c-1 still read the operand tiles
+      if (tid == 0 && !tc::mbar_wait(&mbar, (c - 1) & 1, TC_WAIT_TRIES)) s_ok = 0;
+      __syncthreads();
+      if (!s_ok) break;
+      tc::fence_after_sync();
+    }
+    const float2* Ms = raw + (c & 1) * raw_elems;
+    const float2* Ts = Ms + raw_ms;
+    for (int it = tid; it < TC_RT * 16; it += TC_THREADS) {
+      const int r = it % TC_RT, p = it / TC_RT;
+      float2 g0, g1;
+      if (!TRANS) {
+        g0 = Ms[r * (TC_KC + 1) + 2 * p];
+        g1 = Ms[r * (TC_KC + 1) + 2 * p + 1];
+      } else {
+        g0 = Ms[(2 * p) * (TC_RT + 1) + r];
+        g1 = Ms[(2 * p + 1) * (TC_RT + 1) + r];
+        g0.y = -g0.y;
+        g1.y = -g1.y;
+      }
+      float4 h, l;
+      tc::split_tf32(g0.x, h.x, l.x);
+      tc::split_tf32(g0.y, h.y, l.y);
+      tc::split_tf32(g1.x, h.z, l.z);
+      tc::split_tf32(g1.y, h.w, l.w);
+      const uint32_t off = (uint32_t)(r >> 3) * TC_SBO + (uint32_t)p * TC_LBO + (uint32_t)(r & 7) * 16;
+      *reinterpret_cast<float4*>(A_hi + off) = h;
+      *reinterpret_cast<float4*>(A_lo + off) = l;
+    }
+    for (int it = tid; it < kp * 16; it += TC_THREADS) {
+      const int j = it % kp, p = it / kp;
+      const float2 t0 = Ts[(2 * p) * kp + j], t1 = Ts[(2 * p + 1) * kp + j];
+      float4 h0, l0, h1, l1;
+      tc::split_tf32(t0.x, h0.x, l0.x);
+      tc::split_tf32(-t0.y, h0.y, l0.y);
+      tc::split_tf32(t1.x, h0.z, l0.z);
+      tc::split_tf32(-t1.y, h0.w, l0.w);
+      h1 = make_float4(-h0.y, h0.x, -h0.w, h0.z);
+      l1 = make_float4(-l0.y, l0.x, -l0.w, l0.z);
+      const int n0 = 2 * j, n1 = 2 * j + 1;
+      const uint32_t o0 = (uint32_t)(n0 >> 3) * TC_SBO + (uint32_t)p * TC_LBO + (uint32_t)(n0 & 7) * 16;
+      const uint32_t o1 = (uint32_t)(n1 >> 3) * TC_SBO + (uint32_t)p * TC_LBO + (uint32_t)(n1 & 7) * 16;
+      *reinterpret_cast<float4*>(B_hi + o0) = h0;
+      *reinterpret_cast<float4*>(B_lo + o0) = l0;
+      *reinterpret_cast<float4*>(B_hi + o1) = h1;
+      *reinterpret_cast<float4*>(B_lo + o1) = l1;
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t a_hi = tc::smem_u32(A_hi), a_lo = tc::smem_u32(A_lo);
+      const uint32_t b_hi = tc::smem_u32(B_hi), b_lo = tc::smem_u32(B_lo);
+#pragma unroll
+      for (int prod = 0; prod < 3; ++prod) {
+        const uint32_t ab = prod == 2 ? a_lo : a_hi;
+        const uint32_t bb = prod == 1 ? b_lo : b_hi;
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks) {
+          const uint64_t ad = tc::smem_desc(ab + ks * 2 * TC_LBO, TC_LBO, TC_SBO);
+          const uint64_t bd = tc::smem_desc(bb + ks * 2 * TC_LBO, TC_LBO, TC_SBO);
+          tc::mma_tf32(tmem, ad, bd, idesc, (c > 0 || prod > 0 || ks > 0) ? 1u : 0u);
+        }
+      }
+      tc::mma_commit(&mbar);
+    }
+  }
+  cp_async_wait<0>();
+  if (s_ok) {
+    if (tid == 0 && !tc::mbar_wait(&mbar, (nch - 1) & 1, TC_WAIT_TRIES)) s_ok = 0;
+    __syncthreads();
+  }
+  tc::fence_after_sync();
+  if (s_ok && warp < 4) {
+    const int r = r0 + warp * 32 + lane;
+    for (int cc = 0; cc < N / 16; ++cc) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 16), v);
+      if (r >= b) continue;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int j = cc * 8 + t;
+        if (j >= k) continue;
+        const float2 a = make_float2(v[2 * t], v[2 * t + 1]);
+        if (EPI == EPI_TMP) {
+          tmp[(size_t)f * tstride + (size_t)r * k + j] = a;
+        } else {
+          const size_t idx = (size_t)f * NK + ((size_t)ob * b + r) * k + j;
+          if (EPI == EPI_STORE) out[idx] = a;
+          else out[idx] = csub(out[idx], a);
+        }
+      }
+    }
+  }
+  if (!s_ok && tid == 0) atomicExch(err, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core sweep step fed by TMA, with the contraction split over KS CTAs.
+//
+// Same arithmetic as sweep_tc_kernel.  The raw 128 x 32 complex tiles of
+// G_i (or of G_i^H) arrive by 3-D TMA (one tensor map over all factors,
+// coordinate 2 = problem * nx + column) into a 3-stage ring guarded by
+// mbarriers; the CTA's thread 0 refills a stage as soon as it has been
+// split into the TF32 hi/lo operand tiles.  CTA (row tile, part) handles the
+// chunks [part*cpp, (part+1)*cpp) of the contraction and writes a partial
+// 128 x k block; sweep_combine_kernel adds the KS partials in a fixed order
+// and applies the step's epilogue.  All waits are bounded (flag *err).
+constexpr int TC2_STAGES = 3;
+constexpr uint32_t TC2_TILE_BYTES = TC_RT * TC_KC * 8;  // 32 KB raw tile
+
+// one stage: the raw G tile followed by the 32 x k right-hand-side rows
+__host__ __device__ constexpr uint32_t tc2_stage_bytes(int kp) {
+  return (TC2_TILE_BYTES + (uint32_t)TC_KC * kp * 8 + 1023u) & ~1023u;
+}
+__host__ __device__ constexpr size_t tc2_smem_bytes(int kp) {
+  return 2 * 32768 + 2 * (size_t)(2 * kp / 8) * TC_SBO + (size_t)TC2_STAGES * tc2_stage_bytes(kp);
+}
+
+template <bool TRANS>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp, int blk,
+                 int nx, int nrt, int cpp, const float2* rhs, size_t rstride,
+                 float2* __restrict__ part, int F, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t full_bar[TC2_STAGES];
+  __shared__ uint64_t mma_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_ok;
+  const int N = 2 * kp;
+  const uint32_t bt_bytes = (uint32_t)(N / 8) * TC_SBO;
+  unsigned char* A_hi = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  unsigned char* A_lo = A_hi + 32768;
+  unsigned char* B_hi = A_lo + 32768;
+  unsigned char* B_lo = B_hi + bt_bytes;
+  unsigned char* raw = B_lo + bt_bytes;  // TC2_STAGES stages, 1 KB aligned
+  const uint32_t stage_bytes = tc2_stage_bytes(kp);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int f = blockIdx.y;
+  const int rt = blockIdx.x % nrt, ks = blockIdx.x / nrt;
+  const int r0 = rt * TC_RT;
+  const int nch = (b + TC_KC - 1) / TC_KC;
+  const int c_begin = ks * cpp, c_end = min(nch, c_begin + cpp);
+  const int nloc = c_end - c_begin;
+  const int zblk = f * nx + blk;
+  const float2* rf = rhs + (size_t)f * rstride;
+  const uint32_t ncols = N <= 32 ? 32u : (N <= 64 ? 64u : 128u);
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, ncols);
+  if (tid == 0) {
+    for (int s = 0; s < TC2_STAGES; ++s) tc::mbar_init(&full_bar[s], 1);
+    tc::mbar_init(&mma_bar, 1);
+    s_ok = 1;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  auto issue = [&](int lc) {  // thread 0: TMA of local chunk lc into its stage
+    const int s = lc % TC2_STAGES;
+    const int m0 = (c_begin + lc) * TC_KC;
+    const uint32_t rhs_bytes = (uint32_t)(min(TC_KC, b - m0) * k * 8);
+    unsigned char* st = raw + s * stage_bytes;
+    tc::mbar_expect_tx(&full_bar[s], TC2_TILE_BYTES + rhs_bytes);
+    if (!TRANS) tc::tma_load_3d(st, &tmap, 2 * m0, r0, zblk, &full_bar[s]);
+    else tc::tma_load_3d(st, &tmap, 2 * r0, m0, zblk, &full_bar[s]);
+    tc::bulk_load(st + TC2_TILE_BYTES, rf + (size_t)m0 * k, rhs_bytes, &full_bar[s]);
+  };
+  if (tid == 0)
+    for (int lc = 0; lc < TC2_STAGES && lc < nloc; ++lc) issue(lc);
+
+  const uint32_t idesc = tc::idesc_tf32(TC_RT, N);
+  int consumed = 0;  // chunks whose TMA has been waited for
+  for (int lc = 0; lc < nloc; ++lc) {
+    const int s = lc % TC2_STAGES;
+    if (tid == 0) {
+      if (!tc::mbar_wait(&full_bar[s], (lc / TC2_STAGES) & 1, TC_WAIT_TRIES)) s_ok = 0;
+      if (lc > 0 && s_ok && !tc::mbar_wait(&mma_bar, (lc - 1) & 1, TC_WAIT_TRIES)) s_ok = 0;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    consumed = lc + 1;
+    tc::fence_after_sync();
+    const float* R = reinterpret_cast<const float*>(raw + s * stage_bytes);
+    const float2* Rt = reinterpret_cast<const float2*>(raw + s * stage_bytes + TC2_TILE_BYTES);
+    // split the raw tile into the K-major hi/lo operand tiles (rotated item
+    // order keeps both the 16-byte reads and the 16-byte writes conflict-free)
+    for (int it = tid; it < TC_RT * 16; it += TC_THREADS) {
+      const int r = (it & 7) + 8 * (it >> 7);
+      const int p = (((it >> 3) & 15) + r) & 15;
+      float4 g;
+      if (!TRANS) {
+        g = *reinterpret_cast<const float4*>(R + r * 64 + 4 * p);
+      } else {
+        const float2 a = *reinterpret_cast<const float2*>(R + (2 * p) * 256 + 2 * r);
+        const float2 c = *reinterpret_cast<const float2*>(R + (2 * p + 1) * 256 + 2 * r);
+        g = make_float4(a.x, -a.y, c.x, -c.y);
+      }
+      float4 h, l;
+      tc::split_tf32(g.x, h.x, l.x);
+      tc::split_tf32(g.y, h.y, l.y);
+      tc::split_tf32(g.z, h.z, l.z);
+      tc::split_tf32(g.w, h.w, l.w);
+      const uint32_t off = (uint32_t)(r >> 3) * TC_SBO + (uint32_t)p * TC_LBO + (uint32_t)(r & 7) * 16;
+      *reinterpret_cast<float4*>(A_hi + off) = h;
+      *reinterpret_cast<float4*>(A_lo + off) = l;
+    }
+    const int m0 = (c_begin + lc) * TC_KC;
+    for (int it = tid; it < kp * 16; it += TC_THREADS) {
+      const int j = it % kp, p = it / kp;
+      const int ma = m0 + 2 * p, mb = ma + 1;
+      const float2 t0 = (j < k && ma < b) ? Rt[(2 * p) * k + j] : make_float2(0.f, 0.f);
+      const float2 t1 = (j < k && mb < b) ? Rt[(2 * p + 1) * k + j] : make_float2(0.f, 0.f);
+      float4 h0, l0;
+      tc::split_tf32(t0.x, h0.x, l0.x);
+      tc::split_tf32(-t0.y, h0.y, l0.y);
+      tc::split_tf32(t1.x, h0.z, l0.z);
+      tc::split_tf32(-t1.y, h0.w, l0.w);
+      const float4 h1 = make_float4(-h0.y, h0.x, -h0.w, h0.z);
+      const float4 l1 = make_float4(-l0.y, l0.x, -l0.w, l0.z);
+      const int n0 = 2 * j, n1 = 2 * j + 1;
+      const uint32_t o0 = (uint32_t)(n0 >> 3) * TC_SBO + (uint32_t)p * TC_LBO + (uint32_t)(n0 & 7) * 16;
+      const uint32_t o1 = (uint32_t)(n1 >> 3) * TC_SBO + (uint32_t)p * TC_LBO + (uint32_t)(n1 & 7) * 16;
+      *reinterpret_cast<float4*>(B_hi + o0) = h0;
+      *reinterpret_cast<float4*>(B_lo + o0) = l0;
+      *reinterpret_cast<float4*>(B_hi + o1) = h1;
+      *reinterpret_cast<float4*>(B_lo + o1) = l1;
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      if (lc + TC2_STAGES < nloc) issue(lc + TC2_STAGES);  // stage s is free again
+      const uint32_t a_hi = tc::smem_u32(A_hi), a_lo = tc::smem_u32(A_lo);
+      const uint32_t b_hi = tc::smem_u32(B_hi), b_lo = tc::smem_u32(B_lo);
+#pragma unroll
+      for (int prod = 0; prod < 3; ++prod) {
+        const uint32_t ab = prod == 2 ? a_lo : a_hi;
+        const uint32_t bb = prod == 1 ? b_lo : b_hi;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint64_t ad = tc::smem_desc(ab + kk * 2 * TC_LBO, TC_LBO, TC_SBO);
+          const uint64_t bd = tc::smem_desc(bb + kk * 2 * TC_LBO, TC_LBO, TC_SBO);
+          tc::mma_tf32(tmem, ad, bd, idesc, (lc > 0 || prod > 0 || kk > 0) ? 1u : 0u);
+        }
+      }
+      tc::mma_commit(&mma_bar);
+    }
+  }
+  if (s_ok && nloc > 0) {
+    if (tid == 0 && !tc::mbar_wait(&mma_bar, (nloc - 1) & 1, TC_WAIT_TRIES)) s_ok = 0;
+    __syncthreads();
+  }
+  tc::fence_after_sync();
+  if (s_ok && warp < 4) {
+    const int r = r0 + warp * 32 + lane;
+    float2* pf = part + ((size_t)ks * F + f) * (size_t)b * k;
+    for (int cc = 0; cc < N / 16; ++cc) {
+      float v[16];
+      if (nloc > 0) {
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 16), v);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) v[t] = 0.f;
+      }
+      if (r >= b) continue;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int j = cc * 8 + t;
+        if (j < k) pf[(size_t)r * k + j] = make_float2(v[2 * t], v[2 * t + 1]);
+      }
+    }
+  }
+  if (!s_ok && tid == 0) {
+    atomicExch(err, 1);
+    // drain the TMA copies still in flight before the CTA's shared memory goes
+    const int issued = min(nloc, consumed + TC2_STAGES);
+    for (int q = consumed; q < issued; ++q)
+      tc::mbar_wait(&full_bar[q % TC2_STAGES], (q / TC2_STAGES) & 1, TC_WAIT_TRIES);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// Sum the KS partial products in a fixed order and apply the step epilogue.
+template <int EPI>
+__global__ void sweep_combine_kernel(int F, int b, int k, int KS, size_t NK, int ob,
+                                     const float2* __restrict__ part, float2* out, float2* tmp,
+                                     size_t tstride) {
+  const size_t total = (size_t)F * b * k;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    float2 s = part[e];
+    for (int q = 1; q < KS; ++q) s = cadd(s, part[(size_t)q * total + e]);
+    const int f = (int)(e / ((size_t)b * k));
+    const size_t rem = e - (size_t)f * b * k;
+    if (EPI == EPI_TMP) {
+      tmp[(size_t)f * tstride + rem] = s;
+    } else {
+      const size_t idx = (size_t)f * NK + (size_t)ob * b * k + rem;
+      if (EPI == EPI_STORE) out[idx] = s;
+      else out[idx] = csub(out[idx], s);
+    }
+  }
+}
+
 template <typename T> struct SweepCfg;
 template <> struct SweepCfg<float> { static constexpr int KC = 32, ST = 3; };
 template <> struct SweepCfg<double> { static constexpr int KC = 16, ST = 2; };
 
 template <typename T, bool TRANS, int EPI>
-rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, const C_t<T>* Mat,
+rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, const C_t<T>* Mat,
                     size_t mstride, const C_t<T>* rhs, size_t rstride, C_t<T>* out, C_t<T>* tmp,
                     size_t tstride) {
   using C = C_t<T>;
@@ -250,6 +661,66 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, const C_t<T>*
   const int b = d.b, F = fa->F;
   const size_t NK = (size_t)d.n * k;
   cudaStream_t st = fa->stream;
+  if constexpr (std::is_same<T, float>::value) {
+    if (fa->prec == RR_FP32 && kp <= 32 && fa->tma_ok && (k % 2) == 0) {
+      const int nrt = (b + TC_RT - 1) / TC_RT;
+      const int nch = (b + TC_KC - 1) / TC_KC;
+      const int nsm = num_sms(d.device);
+      int KS = (int)std::min<long>(4, std::max<long>(1, (7L * nsm / 2 + nrt * F - 1) / (nrt * F)));
+      KS = std::min(KS, nch);
+      const int cpp = (nch + KS - 1) / KS;
+      KS = (nch + cpp - 1) / cpp;
+      const size_t smem = tc2_smem_bytes(kp) + 1024;
+      static size_t tc2_attr = 0;
+      if (smem > tc2_attr) {
+        RR_CUDA(cudaFuncSetAttribute(sweep_tc2_kernel<TRANS>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tc2_attr = smem;
+      }
+      const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(fa->tmap[TRANS ? 1 : 0]);
+      dim3 grid(nrt * KS, F);
+      prof_begin(PROF_SWEEP, st);
+      sweep_tc2_kernel<TRANS><<<grid, TC_THREADS, smem, st>>>(
+          *tm, b, k, kp, blk, d.nx, nrt, cpp, reinterpret_cast<const float2*>(rhs), rstride,
+          reinterpret_cast<float2*>(fa->Pbuf), F, fa->flag + F);
+      const size_t total = (size_t)F * b * k;
+      const int cblocks = (int)std::min<size_t>((total + 255) / 256, 8192);
+      sweep_combine_kernel<EPI><<<cblocks, 256, 0, st>>>(
+          F, b, k, KS, NK, ob, reinterpret_cast<const float2*>(fa->Pbuf), out, tmp, tstride);
+      prof_end(PROF_SWEEP, st);
+      prof_count(1);
+      RR_CUDA(cudaGetLastError());
+      return RR_OK;
+    }
+    if (fa->prec == RR_FP32 && kp <= 32) {
+      const size_t smem = tc_smem_bytes(kp, TRANS) + 1024;
+      static size_t tc_attr = 0;  // dynamic shared memory opted in so far
+      if (smem > tc_attr) {
+        RR_CUDA(cudaFuncSetAttribute(sweep_tc_kernel<TRANS, EPI>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tc_attr = smem;
+      }
+      dim3 grid((b + TC_RT - 1) / TC_RT, F);
+      prof_begin(PROF_SWEEP, st);
+      sweep_tc_kernel<TRANS, EPI><<<grid, TC_THREADS, smem, st>>>(
+          b, k, kp, NK, ob, Mat, mstride, rhs, rstride, out, tmp, tstride, fa->flag + F);
+      prof_end(PROF_SWEEP, st);
+      cudaError_t le = cudaGetLastError();
+      if (le != cudaSuccess) {
+        cudaFuncAttributes fat;
+        cudaFuncGetAttributes(&fat, sweep_tc_kernel<TRANS, EPI>);
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "sweep_tc launch (grid %u x %u, smem %zu, static %zu, max dyn %d, regs %d, "
+                 "max threads %d): %s",
+                 grid.x, grid.y, smem, fat.sharedSizeBytes, fat.maxDynamicSharedSizeBytes,
+                 fat.numRegs, fat.maxThreadsPerBlock, cudaGetErrorString(le));
+        set_error(buf);
+        return RR_ERR_CUDA;
+      }
+      return RR_OK;
+    }
+  }
   static bool attr_set = false;
   if (!attr_set) {
     RR_CUDA(cudaFuncSetAttribute(sweep_step_kernel<T, TRANS, EPI, KC, ST>,
@@ -303,13 +774,13 @@ rr_status solve_impl(rr_factors* fa, int k, int adjoint, const void* bv, void* x
         rhs = tb;
         rstride = tstride;
       }
-      if ((s = gemm_step<T, false, EPI_STORE>(fa, k, kp, RT, i, G + i * bb, gstride, rhs, rstride,
+      if ((s = gemm_step<T, false, EPI_STORE>(fa, k, kp, RT, i, i, G + i * bb, gstride, rhs, rstride,
                                              x, nullptr, 0)) != RR_OK)
         return s;
     }
     for (int i = nx - 2; i >= 0; --i) {
       stage_rhs<T, BWD>(fa, i, k, nullptr, x, tb);
-      if ((s = gemm_step<T, false, EPI_SUB>(fa, k, kp, RT, i, G + i * bb, gstride, tb, tstride, x,
+      if ((s = gemm_step<T, false, EPI_SUB>(fa, k, kp, RT, i, i, G + i * bb, gstride, tb, tstride, x,
                                            nullptr, 0)) != RR_OK)
         return s;
     }
@@ -320,7 +791,7 @@ rr_status solve_impl(rr_factors* fa, int k, int adjoint, const void* bv, void* x
     const size_t total = (size_t)F * b * k;
     const int blocks = (int)std::min<size_t>((total + 255) / 256, 8192);
     for (int i = 0; i + 1 < nx; ++i) {
-      if ((s = gemm_step<T, true, EPI_TMP>(fa, k, kp, RT, 0, G + i * bb, gstride,
+      if ((s = gemm_step<T, true, EPI_TMP>(fa, k, kp, RT, 0, i, G + i * bb, gstride,
                                           h + (size_t)i * b * k, NK, nullptr, tb2, tstride)) !=
           RR_OK)
         return s;
@@ -335,7 +806,7 @@ rr_status solve_impl(rr_factors* fa, int k, int adjoint, const void* bv, void* x
         rhs = tb;
         rstride = tstride;
       }
-      if ((s = gemm_step<T, true, EPI_STORE>(fa, k, kp, RT, i, G + i * bb, gstride, rhs, rstride,
+      if ((s = gemm_step<T, true, EPI_STORE>(fa, k, kp, RT, i, i, G + i * bb, gstride, rhs, rstride,
                                             x, nullptr, 0)) != RR_OK)
         return s;
     }

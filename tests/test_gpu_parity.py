@@ -94,7 +94,7 @@ SOLVE_CASES = [
 
 
 @pytest.mark.parametrize("name,gf,how", SOLVE_CASES)
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_simt"])
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_solve_matches_oracle(env, name, gf, how, precision, adjoint):
     torch, rr = env
@@ -121,7 +121,7 @@ def test_solve_matches_oracle(env, name, gf, how, precision, adjoint):
     assert info["refine_residual"] <= 1e-12
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_simt"])
 @pytest.mark.parametrize("orthogonalize", [False, True])
 def test_algorithm1_matches_oracle(env, precision, orthogonalize):
     """Sketch, QR, adjoint solve, small SVD, recovery: sigma, sigma_halko, U, V."""
@@ -237,3 +237,31 @@ def test_refinement_reports_non_convergence(env):
     from paper_1902_01458_gb300._lib import rr_solve
     st, _ = rr_solve(fa.handle, b, x, False, 1e-30, 1)
     assert st == 4
+
+
+@pytest.mark.parametrize("grid_shape", [(24, 20), (9, 40), (8, 50)])
+@pytest.mark.parametrize("k", [3, 16, 32])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_tensor_core_sweeps_match_cuda_core_sweeps(env, grid_shape, k, adjoint):
+    """One unrefined FP32 solve: tcgen05 (3xTF32) sweeps against FP32 CUDA-core
+    sweeps on the same factors' precision, and both against the FP64 oracle."""
+    torch, rr = env
+    g = W.ns_grid(*grid_shape)
+    flow = W.smooth_random_flow(g, 2)
+    L = op.assemble(g, flow)
+    o = rr.Operator(g, flow)
+    shifts = np.array([0.6j, 2.2j])
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal((2, g.n, k)) + 1j * rng.standard_normal((2, g.n, k))
+    bd = to_dev(b, torch)
+    xs = {}
+    for prec in ("fp32", "fp32_simt"):
+        fa = o.factor(shifts, prec)
+        x, _ = fa.solve(bd, adjoint=adjoint, refine_tol=0.0, max_refine=0)
+        xs[prec] = x.cpu().numpy()
+        fa.close()
+    assert rel_err(xs["fp32"], xs["fp32_simt"]) < 1e-4
+    for f, s in enumerate(shifts):
+        A = op.shifted(L, s).toarray()
+        want = np.linalg.solve(A.conj().T if adjoint else A, b[f])
+        assert rel_err(xs["fp32"][f], want) < 1e-4
