@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--batch", type=int, default=32, help="frequencies per step per GPU")
+    p.add_argument("--batch", type=int, default=64, help="frequencies per step per GPU")
     p.add_argument("--fp64-batch", type=int, default=2)
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")

@@ -314,7 +314,7 @@ rr_status cholqr2(rr_factors* fa, int k, double2* Y, double2* Rout, Work& w, rr_
 }  // namespace
 
 // TMA tensor maps over all FP32 factors G [F][nx][b][b] (complex, viewed as
-// floats [F*nx][b][2b]): tiles of 128 rows x 32 complex (G) and of 32 rows x
+// floats [F*nx][b][2b]): tiles of 128 rows x 16 complex (G) and of 16 rows x
 // 128 complex (for G^H).  Used only when b >= 128 and the row pitch is a
 // multiple of 16 bytes (b even); otherwise the sweeps use cp.async kernels.
 static int encode_factor_maps(rr_factors* fa) {
@@ -334,7 +334,7 @@ static int encode_factor_maps(rr_factors* fa) {
   }
   const cuuint64_t dims[3] = {(cuuint64_t)2 * d.b, (cuuint64_t)d.b, (cuuint64_t)fa->F * d.nx};
   const cuuint64_t strides[2] = {(cuuint64_t)2 * d.b * 4, (cuuint64_t)2 * d.b * d.b * 4};
-  const cuuint32_t boxN[3] = {64, 128, 1}, boxT[3] = {256, 32, 1}, es[3] = {1, 1, 1};
+  const cuuint32_t boxN[3] = {32, 128, 1}, boxT[3] = {256, 16, 1}, es[3] = {1, 1, 1};
   CUresult r1 = encode(reinterpret_cast<CUtensorMap*>(fa->tmap[0]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                        3, fa->G, dims, strides, boxN, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -531,10 +531,15 @@ extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts
   e = cudaMemsetAsync(fa->flag, 0, (nshift + 1) * sizeof(int), st);
   if (e != cudaSuccess) return fail(cuda_status(e, "rr_factor flags"));
   if ((s = launch_factor(fa)) != RR_OK) return fail(s);
-  std::vector<int> flags(nshift);
-  e = cudaMemcpyAsync(flags.data(), fa->flag, nshift * sizeof(int), cudaMemcpyDeviceToHost, st);
+  std::vector<int> flags(nshift + 1);
+  e = cudaMemcpyAsync(flags.data(), fa->flag, (nshift + 1) * sizeof(int), cudaMemcpyDeviceToHost,
+                      st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(cuda_status(e, "rr_factor"));
+  if (flags[nshift]) {
+    g_err = "rr_factor: a tensor-core update kernel timed out waiting for its MMAs";
+    return fail(RR_ERR_TIMEOUT);
+  }
   *out = fa;
   for (int f = 0; f < nshift; ++f)
     if (flags[f]) {
@@ -708,9 +713,13 @@ extern "C" rr_status rr_refactor(rr_factors* fa, const double* shifts) {
   RR_CUDA(cudaMemsetAsync(fa->flag, 0, (F + 1) * sizeof(int), st));
   rr_status s = launch_factor(fa);
   if (s != RR_OK) return s;
-  std::vector<int> flags(F);
-  RR_CUDA(cudaMemcpyAsync(flags.data(), fa->flag, F * sizeof(int), cudaMemcpyDeviceToHost, st));
+  std::vector<int> flags(F + 1);
+  RR_CUDA(cudaMemcpyAsync(flags.data(), fa->flag, (F + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
+  if (flags[F]) {
+    g_err = "rr_refactor: a tensor-core update kernel timed out waiting for its MMAs";
+    return RR_ERR_TIMEOUT;
+  }
   for (int f = 0; f < F; ++f)
     if (flags[f]) {
       g_err = "rr_refactor: exact zero pivot";

@@ -438,187 +438,247 @@ sweep_tc_kernel(int b, int k, int kp, size_t NK, int ob, const float2* __restric
 // ---------------------------------------------------------------------------
 // Tensor-core sweep step fed by TMA, with the contraction split over KS CTAs.
 //
-// Same arithmetic as sweep_tc_kernel.  The raw 128 x 32 complex tiles of
-// G_i (or of G_i^H) arrive by 3-D TMA (one tensor map over all factors,
-// coordinate 2 = problem * nx + column) into a 3-stage ring guarded by
-// mbarriers; the CTA's thread 0 refills a stage as soon as it has been
-// split into the TF32 hi/lo operand tiles.  CTA (row tile, part) handles the
-// chunks [part*cpp, (part+1)*cpp) of the contraction and writes a partial
-// 128 x k block; sweep_combine_kernel adds the KS partials in a fixed order
-// and applies the step's epilogue.  All waits are bounded (flag *err).
-constexpr int TC2_STAGES = 3;
-constexpr uint32_t TC2_TILE_BYTES = TC_RT * TC_KC * 8;  // 32 KB raw tile
+// Same arithmetic as sweep_tc_kernel, on chunks of 16 complex columns.  The
+// raw 128 x 16 complex tiles of G_i (or of G_i^H) arrive by 3-D TMA (one
+// tensor map over all factors, coordinate 2 = problem * nx + column), and the
+// matching 16 right-hand-side rows by a 1-D bulk copy, into a 4-stage ring
+// guarded by mbarriers.  The split into TF32 hi/lo operand tiles is
+// double-buffered so the tensor core works on chunk c while the threads
+// split chunk c+1.  CTA (row tile, part) handles the chunks
+// [part*cpp, (part+1)*cpp) and writes a partial 128 x k block;
+// sweep_combine_kernel adds the KS partials in a fixed order and applies the
+// step's epilogue.  All waits are bounded (flag *err).
+constexpr int TC2_KC = 16;                                // complex columns per chunk
+constexpr int TC2_STAGES = 4;
+constexpr uint32_t TC2_SBO = 1024;                        // 32 reals of K per 8-row group
+constexpr uint32_t TC2_TILE_BYTES = TC_RT * TC2_KC * 8;   // 16 KB raw tile
+constexpr uint32_t TC2_A_BYTES = TC_RT * 2 * TC2_KC * 4;  // 16 KB operand tile
 
-// one stage: the raw G tile followed by the 32 x k right-hand-side rows
 __host__ __device__ constexpr uint32_t tc2_stage_bytes(int kp) {
-  return (TC2_TILE_BYTES + (uint32_t)TC_KC * kp * 8 + 1023u) & ~1023u;
+  return (TC2_TILE_BYTES + (uint32_t)TC2_KC * kp * 8 + 1023u) & ~1023u;
 }
+__host__ __device__ constexpr uint32_t tc2_b_bytes(int kp) { return (uint32_t)(2 * kp / 8) * TC2_SBO; }
 __host__ __device__ constexpr size_t tc2_smem_bytes(int kp) {
-  return 2 * 32768 + 2 * (size_t)(2 * kp / 8) * TC_SBO + (size_t)TC2_STAGES * tc2_stage_bytes(kp);
+  return 2 * (2 * (size_t)TC2_A_BYTES + 2 * (size_t)tc2_b_bytes(kp)) +
+         (size_t)TC2_STAGES * tc2_stage_bytes(kp);
 }
+
+__device__ __forceinline__ bool tc_poll(uint64_t* bar, uint32_t parity) {
+  return tc::mbar_wait(bar, parity, TC_WAIT_TRIES);
+}
+
+constexpr int TC2_CONV = 256;                 // converter threads (warps 0-7)
+constexpr int TC2_THREADS = TC2_CONV + 32;    // + control warp 8 (TMA producer, MMA issuer)
 
 template <bool TRANS>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC2_THREADS, 1)
 sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp, int blk,
-                 int nx, int nrt, int cpp, const float2* rhs, size_t rstride,
+                 int nx, int nrt, int KS, int cpp, const float2* rhs, size_t rstride,
                  float2* __restrict__ part, int F, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t full_bar[TC2_STAGES];
-  __shared__ uint64_t mma_bar;
+  __shared__ uint64_t mma_bar[2];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_ok;
   const int N = 2 * kp;
-  const uint32_t bt_bytes = (uint32_t)(N / 8) * TC_SBO;
-  unsigned char* A_hi = reinterpret_cast<unsigned char*>(
+  const uint32_t bt_bytes = tc2_b_bytes(kp);
+  const uint32_t buf_bytes = 2 * TC2_A_BYTES + 2 * bt_bytes;  // hi/lo A and B of one chunk
+  unsigned char* ops = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  unsigned char* A_lo = A_hi + 32768;
-  unsigned char* B_hi = A_lo + 32768;
-  unsigned char* B_lo = B_hi + bt_bytes;
-  unsigned char* raw = B_lo + bt_bytes;  // TC2_STAGES stages, 1 KB aligned
+  unsigned char* raw = ops + 2 * buf_bytes;  // TC2_STAGES stages, 1 KB aligned
   const uint32_t stage_bytes = tc2_stage_bytes(kp);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int f = blockIdx.y;
-  const int rt = blockIdx.x % nrt, ks = blockIdx.x / nrt;
-  const int r0 = rt * TC_RT;
-  const int nch = (b + TC_KC - 1) / TC_KC;
-  const int c_begin = ks * cpp, c_end = min(nch, c_begin + cpp);
-  const int nloc = c_end - c_begin;
-  const int zblk = f * nx + blk;
-  const float2* rf = rhs + (size_t)f * rstride;
-  const uint32_t ncols = N <= 32 ? 32u : (N <= 64 ? 64u : 128u);
+  const bool ctrl = (tid == TC2_CONV);  // the one thread that feeds TMA and the tensor core
+  const int nch = (b + TC2_KC - 1) / TC2_KC;
+  const int nitems = nrt * KS * F;
+  const int my_items = nitems > (int)blockIdx.x
+                           ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                           : 0;
+  // Per K step two MMAs: A_hi x [B_hi | B_lo] (N = 2 * 2k, both hi products
+  // in one pass over A_hi) and A_lo x B_hi.  Two accumulator sets (even and
+  // odd K steps) keep consecutive MMAs independent; the epilogue adds the
+  // four partial sums.  Set layout: [hi.hi | hi.lo | lo.hi], 3N columns.
+  const uint32_t ncols = (N <= 32) ? 256u : 512u;
+  // work item t of this CTA -> (problem, row tile, contraction part)
+  auto item = [&](int t, int& f, int& rt, int& ks) {
+    const int it = (int)blockIdx.x + t * (int)gridDim.x;
+    rt = it % nrt;
+    ks = (it / nrt) % KS;
+    f = it / (nrt * KS);
+  };
+  auto item_len = [&](int ks) { return min(nch, ks * cpp + cpp) - ks * cpp; };
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, ncols);
   if (tid == 0) {
     for (int s = 0; s < TC2_STAGES; ++s) tc::mbar_init(&full_bar[s], 1);
-    tc::mbar_init(&mma_bar, 1);
-    s_ok = 1;
+    tc::mbar_init(&mma_bar[0], 1);
+    tc::mbar_init(&mma_bar[1], 1);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
+  const uint32_t set_cols = (uint32_t)(3 * N <= 128 ? 128 : 256);  // one accumulator set
 
-  auto issue = [&](int lc) {  // thread 0: TMA of local chunk lc into its stage
-    const int s = lc % TC2_STAGES;
-    const int m0 = (c_begin + lc) * TC_KC;
-    const uint32_t rhs_bytes = (uint32_t)(min(TC_KC, b - m0) * k * 8);
+  // control thread: the stream of chunks of all this CTA's items
+  int p_item = 0, p_lc = 0, issued = 0, p_f = 0, p_rt = 0, p_ks = 0, p_len = 0;
+  if (ctrl && my_items > 0) {
+    item(0, p_f, p_rt, p_ks);
+    p_len = item_len(p_ks);
+  }
+  auto issue_next = [&]() {
+    if (p_item >= my_items) return;
+    const int m0 = (p_ks * cpp + p_lc) * TC2_KC;
+    const int s = issued % TC2_STAGES;
+    const uint32_t rhs_bytes = (uint32_t)(min(TC2_KC, b - m0) * k * 8);
     unsigned char* st = raw + s * stage_bytes;
+    const int zblk = p_f * nx + blk;
     tc::mbar_expect_tx(&full_bar[s], TC2_TILE_BYTES + rhs_bytes);
-    if (!TRANS) tc::tma_load_3d(st, &tmap, 2 * m0, r0, zblk, &full_bar[s]);
-    else tc::tma_load_3d(st, &tmap, 2 * r0, m0, zblk, &full_bar[s]);
-    tc::bulk_load(st + TC2_TILE_BYTES, rf + (size_t)m0 * k, rhs_bytes, &full_bar[s]);
-  };
-  if (tid == 0)
-    for (int lc = 0; lc < TC2_STAGES && lc < nloc; ++lc) issue(lc);
-
-  const uint32_t idesc = tc::idesc_tf32(TC_RT, N);
-  int consumed = 0;  // chunks whose TMA has been waited for
-  for (int lc = 0; lc < nloc; ++lc) {
-    const int s = lc % TC2_STAGES;
-    if (tid == 0) {
-      if (!tc::mbar_wait(&full_bar[s], (lc / TC2_STAGES) & 1, TC_WAIT_TRIES)) s_ok = 0;
-      if (lc > 0 && s_ok && !tc::mbar_wait(&mma_bar, (lc - 1) & 1, TC_WAIT_TRIES)) s_ok = 0;
-    }
-    __syncthreads();
-    if (!s_ok) break;
-    consumed = lc + 1;
-    tc::fence_after_sync();
-    const float* R = reinterpret_cast<const float*>(raw + s * stage_bytes);
-    const float2* Rt = reinterpret_cast<const float2*>(raw + s * stage_bytes + TC2_TILE_BYTES);
-    // split the raw tile into the K-major hi/lo operand tiles (rotated item
-    // order keeps both the 16-byte reads and the 16-byte writes conflict-free)
-    for (int it = tid; it < TC_RT * 16; it += TC_THREADS) {
-      const int r = (it & 7) + 8 * (it >> 7);
-      const int p = (((it >> 3) & 15) + r) & 15;
-      float4 g;
-      if (!TRANS) {
-        g = *reinterpret_cast<const float4*>(R + r * 64 + 4 * p);
-      } else {
-        const float2 a = *reinterpret_cast<const float2*>(R + (2 * p) * 256 + 2 * r);
-        const float2 c = *reinterpret_cast<const float2*>(R + (2 * p + 1) * 256 + 2 * r);
-        g = make_float4(a.x, -a.y, c.x, -c.y);
+    if (!TRANS) tc::tma_load_3d(st, &tmap, 2 * m0, p_rt * TC_RT, zblk, &full_bar[s]);
+    else tc::tma_load_3d(st, &tmap, 2 * p_rt * TC_RT, m0, zblk, &full_bar[s]);
+    tc::bulk_load(st + TC2_TILE_BYTES, rhs + (size_t)p_f * rstride + (size_t)m0 * k, rhs_bytes,
+                  &full_bar[s]);
+    ++issued;
+    if (++p_lc == p_len) {
+      p_lc = 0;
+      if (++p_item < my_items) {
+        item(p_item, p_f, p_rt, p_ks);
+        p_len = item_len(p_ks);
       }
-      float4 h, l;
-      tc::split_tf32(g.x, h.x, l.x);
-      tc::split_tf32(g.y, h.y, l.y);
-      tc::split_tf32(g.z, h.z, l.z);
-      tc::split_tf32(g.w, h.w, l.w);
-      const uint32_t off = (uint32_t)(r >> 3) * TC_SBO + (uint32_t)p * TC_LBO + (uint32_t)(r & 7) * 16;
-      *reinterpret_cast<float4*>(A_hi + off) = h;
-      *reinterpret_cast<float4*>(A_lo + off) = l;
     }
-    const int m0 = (c_begin + lc) * TC_KC;
-    for (int it = tid; it < kp * 16; it += TC_THREADS) {
-      const int j = it % kp, p = it / kp;
-      const int ma = m0 + 2 * p, mb = ma + 1;
-      const float2 t0 = (j < k && ma < b) ? Rt[(2 * p) * k + j] : make_float2(0.f, 0.f);
-      const float2 t1 = (j < k && mb < b) ? Rt[(2 * p + 1) * k + j] : make_float2(0.f, 0.f);
-      float4 h0, l0;
-      tc::split_tf32(t0.x, h0.x, l0.x);
-      tc::split_tf32(-t0.y, h0.y, l0.y);
-      tc::split_tf32(t1.x, h0.z, l0.z);
-      tc::split_tf32(-t1.y, h0.w, l0.w);
-      const float4 h1 = make_float4(-h0.y, h0.x, -h0.w, h0.z);
-      const float4 l1 = make_float4(-l0.y, l0.x, -l0.w, l0.z);
-      const int n0 = 2 * j, n1 = 2 * j + 1;
-      const uint32_t o0 = (uint32_t)(n0 >> 3) * TC_SBO + (uint32_t)p * TC_LBO + (uint32_t)(n0 & 7) * 16;
-      const uint32_t o1 = (uint32_t)(n1 >> 3) * TC_SBO + (uint32_t)p * TC_LBO + (uint32_t)(n1 & 7) * 16;
-      *reinterpret_cast<float4*>(B_hi + o0) = h0;
-      *reinterpret_cast<float4*>(B_lo + o0) = l0;
-      *reinterpret_cast<float4*>(B_hi + o1) = h1;
-      *reinterpret_cast<float4*>(B_lo + o1) = l1;
+  };
+  if (ctrl)
+    for (int q = 0; q < TC2_STAGES; ++q) issue_next();
+  // operand descriptors of both buffers; a K step of 8 advances 256 bytes
+  uint64_t dA[2][2], dB[2][2];
+  if (ctrl)
+    for (int q = 0; q < 2; ++q) {
+      const uint32_t a0 = tc::smem_u32(ops + q * buf_bytes);
+      dA[q][0] = tc::smem_desc(a0, TC_LBO, TC2_SBO);
+      dA[q][1] = tc::smem_desc(a0 + TC2_A_BYTES, TC_LBO, TC2_SBO);
+      dB[q][0] = tc::smem_desc(a0 + 2 * TC2_A_BYTES, TC_LBO, TC2_SBO);
+      dB[q][1] = tc::smem_desc(a0 + 2 * TC2_A_BYTES + bt_bytes, TC_LBO, TC2_SBO);
     }
-    tc::fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      if (lc + TC2_STAGES < nloc) issue(lc + TC2_STAGES);  // stage s is free again
-      const uint32_t a_hi = tc::smem_u32(A_hi), a_lo = tc::smem_u32(A_lo);
-      const uint32_t b_hi = tc::smem_u32(B_hi), b_lo = tc::smem_u32(B_lo);
+
+  const uint32_t idesc_hi = tc::idesc_tf32(TC_RT, 2 * N);
+  const uint32_t idesc_lo = tc::idesc_tf32(TC_RT, N);
+  int g = 0;  // chunks consumed so far (global over this CTA's items)
+  bool failed = false;
+  for (int t = 0; t < my_items && !failed; ++t) {
+    int f, rt, ks;
+    item(t, f, rt, ks);
+    const int nl = item_len(ks);
+    for (int lc = 0; lc < nl; ++lc, ++g) {
+      const int s = g % TC2_STAGES, q = g & 1;
+      bool ok = true;
+      if (tid < TC2_CONV) {
+        ok = tc_poll(&full_bar[s], (g / TC2_STAGES) & 1);
+        if (ok && g >= 2) ok = tc_poll(&mma_bar[q], ((g - 2) >> 1) & 1);  // buffer q is free
+        tc::fence_after_sync();
+        unsigned char* A_hi = ops + q * buf_bytes;
+        unsigned char* A_lo = A_hi + TC2_A_BYTES;
+        unsigned char* B_hi = A_lo + TC2_A_BYTES;
+        unsigned char* B_lo = B_hi + bt_bytes;
+        const float* R = reinterpret_cast<const float*>(raw + s * stage_bytes);
+        const float2* Rt = reinterpret_cast<const float2*>(raw + s * stage_bytes + TC2_TILE_BYTES);
+        if (ok) {
+          // rotated item order keeps the 16-byte reads and writes conflict-free
+          for (int it = tid; it < TC_RT * 8; it += TC2_CONV) {
+            const int r = (it & 7) + 8 * (it >> 6);
+            const int p = (((it >> 3) & 7) + r) & 7;
+            float4 gv;
+            if (!TRANS) {
+              gv = *reinterpret_cast<const float4*>(R + r * 32 + 4 * p);
+            } else {
+              const float2 a = *reinterpret_cast<const float2*>(R + (2 * p) * 256 + 2 * r);
+              const float2 c = *reinterpret_cast<const float2*>(R + (2 * p + 1) * 256 + 2 * r);
+              gv = make_float4(a.x, -a.y, c.x, -c.y);
+            }
+            float4 h, l;
+            tc::split_tf32(gv.x, h.x, l.x);
+            tc::split_tf32(gv.y, h.y, l.y);
+            tc::split_tf32(gv.z, h.z, l.z);
+            tc::split_tf32(gv.w, h.w, l.w);
+            const uint32_t off =
+                (uint32_t)(r >> 3) * TC2_SBO + (uint32_t)p * TC_LBO + (uint32_t)(r & 7) * 16;
+            *reinterpret_cast<float4*>(A_hi + off) = h;
+            *reinterpret_cast<float4*>(A_lo + off) = l;
+          }
+          const int m0 = (ks * cpp + lc) * TC2_KC;
+          for (int it = tid; it < kp * 8; it += TC2_CONV) {
+            const int j = it % kp, p = it / kp;
+            const int ma = m0 + 2 * p, mb = ma + 1;
+            const float2 t0 = (j < k && ma < b) ? Rt[(2 * p) * k + j] : make_float2(0.f, 0.f);
+            const float2 t1 = (j < k && mb < b) ? Rt[(2 * p + 1) * k + j] : make_float2(0.f, 0.f);
+            float4 h0, l0;
+            tc::split_tf32(t0.x, h0.x, l0.x);
+            tc::split_tf32(-t0.y, h0.y, l0.y);
+            tc::split_tf32(t1.x, h0.z, l0.z);
+            tc::split_tf32(-t1.y, h0.w, l0.w);
+            const float4 h1 = make_float4(-h0.y, h0.x, -h0.w, h0.z);
+            const float4 l1 = make_float4(-l0.y, l0.x, -l0.w, l0.z);
+            const int n0 = 2 * j, n1 = 2 * j + 1;
+            const uint32_t o0 =
+                (uint32_t)(n0 >> 3) * TC2_SBO + (uint32_t)p * TC_LBO + (uint32_t)(n0 & 7) * 16;
+            const uint32_t o1 =
+                (uint32_t)(n1 >> 3) * TC2_SBO + (uint32_t)p * TC_LBO + (uint32_t)(n1 & 7) * 16;
+            *reinterpret_cast<float4*>(B_hi + o0) = h0;
+            *reinterpret_cast<float4*>(B_lo + o0) = l0;
+            *reinterpret_cast<float4*>(B_hi + o1) = h1;
+            *reinterpret_cast<float4*>(B_lo + o1) = l1;
+          }
+        }
+        tc::fence_async_smem();
+      }
+      failed = __syncthreads_or(ok ? 0 : 1) != 0;
+      if (failed) break;
+      if (ctrl) {
+        tc::fence_after_sync();
+        issue_next();  // stage s has been split: refill it
 #pragma unroll
-      for (int prod = 0; prod < 3; ++prod) {
-        const uint32_t ab = prod == 2 ? a_lo : a_hi;
-        const uint32_t bb = prod == 1 ? b_lo : b_hi;
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t koff = (uint64_t)(kk * 2 * TC_LBO >> 4);
+          const uint32_t set = tmem + (uint32_t)(kk & 1) * set_cols;
+          const uint32_t acc = (lc > 0 || kk > 1) ? 1u : 0u;
+          tc::mma_tf32(set, dA[q][0] + koff, dB[q][0] + koff, idesc_hi, acc);
+          tc::mma_tf32(set + 2 * N, dA[q][1] + koff, dB[q][0] + koff, idesc_lo, acc);
+        }
+        tc::mma_commit(&mma_bar[q]);
+      }
+    }
+    if (failed) break;
+    // item done: wait for its last MMAs, then move the accumulator to its slot
+    bool ok = (tid < TC2_CONV) ? tc_poll(&mma_bar[(g - 1) & 1], ((g - 1) >> 1) & 1) : true;
+    failed = __syncthreads_or(ok ? 0 : 1) != 0;
+    if (failed) break;
+    tc::fence_after_sync();
+    if (warp < 4) {
+      const int r = rt * TC_RT + warp * 32 + lane;
+      float2* pf = part + ((size_t)ks * F + f) * (size_t)b * k;
+      for (int cc = 0; cc < N / 16; ++cc) {
+        float v[16], w[16];
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 16);
+        tc::tmem_ld16(ta, v);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          const uint64_t ad = tc::smem_desc(ab + kk * 2 * TC_LBO, TC_LBO, TC_SBO);
-          const uint64_t bd = tc::smem_desc(bb + kk * 2 * TC_LBO, TC_LBO, TC_SBO);
-          tc::mma_tf32(tmem, ad, bd, idesc, (lc > 0 || prod > 0 || kk > 0) ? 1u : 0u);
+        for (int a = 1; a < 6; ++a) {  // sets 0/1 x {hi.hi, hi.lo, lo.hi}
+          tc::tmem_ld16(ta + (uint32_t)(a / 3) * set_cols + (uint32_t)(a % 3) * N, w);
+#pragma unroll
+          for (int tt = 0; tt < 16; ++tt) v[tt] += w[tt];
+        }
+        if (r >= b) continue;
+#pragma unroll
+        for (int tt = 0; tt < 8; ++tt) {
+          const int j = cc * 8 + tt;
+          if (j < k) pf[(size_t)r * k + j] = make_float2(v[2 * tt], v[2 * tt + 1]);
         }
       }
-      tc::mma_commit(&mma_bar);
     }
+    tc::fence_before_sync();  // accumulator reads complete before the next item's MMAs
   }
-  if (s_ok && nloc > 0) {
-    if (tid == 0 && !tc::mbar_wait(&mma_bar, (nloc - 1) & 1, TC_WAIT_TRIES)) s_ok = 0;
-    __syncthreads();
-  }
-  tc::fence_after_sync();
-  if (s_ok && warp < 4) {
-    const int r = r0 + warp * 32 + lane;
-    float2* pf = part + ((size_t)ks * F + f) * (size_t)b * k;
-    for (int cc = 0; cc < N / 16; ++cc) {
-      float v[16];
-      if (nloc > 0) {
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 16), v);
-      } else {
-#pragma unroll
-        for (int t = 0; t < 16; ++t) v[t] = 0.f;
-      }
-      if (r >= b) continue;
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int j = cc * 8 + t;
-        if (j < k) pf[(size_t)r * k + j] = make_float2(v[2 * t], v[2 * t + 1]);
-      }
-    }
-  }
-  if (!s_ok && tid == 0) {
+  if (failed && ctrl) {
     atomicExch(err, 1);
-    // drain the TMA copies still in flight before the CTA's shared memory goes
-    const int issued = min(nloc, consumed + TC2_STAGES);
-    for (int q = consumed; q < issued; ++q)
-      tc::mbar_wait(&full_bar[q % TC2_STAGES], (q / TC2_STAGES) & 1, TC_WAIT_TRIES);
+    // drain the copies still in flight before the CTA's shared memory goes
+    for (int qq = g; qq < issued; ++qq)
+      tc::mbar_wait(&full_bar[qq % TC2_STAGES], (qq / TC2_STAGES) & 1, TC_WAIT_TRIES);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -664,12 +724,22 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
   if constexpr (std::is_same<T, float>::value) {
     if (fa->prec == RR_FP32 && kp <= 32 && fa->tma_ok && (k % 2) == 0) {
       const int nrt = (b + TC_RT - 1) / TC_RT;
-      const int nch = (b + TC_KC - 1) / TC_KC;
+      const int nch = (b + TC2_KC - 1) / TC2_KC;
       const int nsm = num_sms(d.device);
-      int KS = (int)std::min<long>(4, std::max<long>(1, (7L * nsm / 2 + nrt * F - 1) / (nrt * F)));
-      KS = std::min(KS, nch);
+      // split count: best balance of items over the persistent CTAs
+      int KS = 1;
+      double best = 0.0;
+      for (int ksc = 1; ksc <= 4 && ksc <= nch; ++ksc) {
+        const int cppc = (nch + ksc - 1) / ksc;
+        const int ksr = (nch + cppc - 1) / cppc;
+        const long items = (long)nrt * F * ksr;
+        const long waves = (items + nsm - 1) / nsm;
+        const double eff = (double)items / (double)(waves * nsm);
+        if (eff > best + 1e-9) { best = eff; KS = ksr; }
+      }
       const int cpp = (nch + KS - 1) / KS;
-      KS = (nch + cpp - 1) / cpp;
+      const int nitems = nrt * F * KS;
+      const int grid_x = std::min(nitems, nsm);
       const size_t smem = tc2_smem_bytes(kp) + 1024;
       static size_t tc2_attr = 0;
       if (smem > tc2_attr) {
@@ -678,10 +748,9 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
         tc2_attr = smem;
       }
       const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(fa->tmap[TRANS ? 1 : 0]);
-      dim3 grid(nrt * KS, F);
       prof_begin(PROF_SWEEP, st);
-      sweep_tc2_kernel<TRANS><<<grid, TC_THREADS, smem, st>>>(
-          *tm, b, k, kp, blk, d.nx, nrt, cpp, reinterpret_cast<const float2*>(rhs), rstride,
+      sweep_tc2_kernel<TRANS><<<grid_x, TC2_THREADS, smem, st>>>(
+          *tm, b, k, kp, blk, d.nx, nrt, KS, cpp, reinterpret_cast<const float2*>(rhs), rstride,
           reinterpret_cast<float2*>(fa->Pbuf), F, fa->flag + F);
       const size_t total = (size_t)F * b * k;
       const int cblocks = (int)std::min<size_t>((total + 255) / 256, 8192);
