@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--ny", type=int, default=256)
     p.add_argument("--k", type=int, default=32)
     p.add_argument("--roofline-class", default="update")
+    # DRAM bytes per launch of the timed kernel from an ncu capture (see profiles/)
+    p.add_argument("--update-traffic", type=float, default=None)
+    p.add_argument("--sweep-traffic", type=float, default=None)
     p.add_argument("--breakdown", action="store_true",
                    help="one extra profiled step with every kernel class timed")
     return p.parse_args()
@@ -306,23 +309,28 @@ def run_ours(args):
     hbm, bf16, src = peaks()
     roof = None
     if cls_n > 0 and cls_ms > 0:
-        avg_s = cls_ms / 1e3 / cls_n
+        # achieved = algorithmic work of the timed region / event time of the
+        # class; per-launch figures are those totals over the launch count
+        tot_s = cls_ms / 1e3
         if args.roofline_class == "update":
             NB = panel_width(8, b)
-            flops = update_flops_per_step(b, nx, NB, F) / (nx * math.ceil(b / NB))
-            ach = flops / avg_s / 1e12
-            roof = {"kernel": "gj_update_kernel<float,32> (trailing rank-32 complex update)",
+            work = update_flops_per_step(b, nx, NB, F) * args.steps
+            ach = work / tot_s / 1e12
+            roof = {"kernel": f"gj_update_kernel<float,{NB}> (trailing rank-{NB} complex update)",
                     "bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / FP32_ALU_PEAK_TFLOPS,
+                    "traffic": args.update_traffic,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                    "algorithmic_per_launch": flops, "avg_launch_us": avg_s * 1e6}
+                    "algorithmic_per_launch": work / cls_n, "launches": cls_n,
+                    "avg_launch_us": tot_s / cls_n * 1e6}
         elif args.roofline_class == "sweep":
-            byts = F * (b * b * 8 + 3 * b * k * 8)
-            ach = byts / avg_s / 1e9
-            roof = {"kernel": "sweep_step_kernel<float> (one streamwise column)",
+            work = F * (b * b * 8 + 3 * b * k * 8) * cls_n
+            ach = work / tot_s / 1e9
+            roof = {"kernel": "sweep_tc2_kernel + combine (one streamwise column, tcgen05)",
                     "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": None, "peak_source": src,
-                    "algorithmic_per_launch": byts, "avg_launch_us": avg_s * 1e6}
+                    "frac": ach / hbm, "traffic": args.sweep_traffic, "peak_source": src,
+                    "algorithmic_per_launch": work / cls_n, "launches": cls_n,
+                    "avg_launch_us": tot_s / cls_n * 1e6}
 
     # FP64 path on a subset of the same frequencies, and sigma error vs it
     fp64 = None
