@@ -15,6 +15,15 @@ Box-Muller transform in FP64:
 
 Omega itself is real N(0, 1) (stored complex with zero imaginary part), or
 diag(Phi) times it for the physics-informed test matrix of Eq. (9).
+
+The other test matrices Sec. II.C names take their entries from the same
+Philox words (counter (n, j, 0, 0)):
+
+* Rademacher (Clarkson & Woodruff 2009): +1 if bit 0 of w0 is 0, else -1;
+* sparse Rademacher with density d in (0, 1] (Achlioptas 2003 for d = 1/3):
+  the entry is nonzero iff w1 < floor(d 2^32), and then +-1/sqrt(d) with the
+  sign of the Rademacher rule, so that every entry has mean 0, variance 1;
+* orthonormal: the Q factor of the Gaussian matrix (built in resolvent.py).
 """
 from __future__ import annotations
 
@@ -70,9 +79,45 @@ def gaussian(seed: int, n_rows: int, k: int) -> np.ndarray:
     return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
 
 
-def test_matrix(seed: int, n_rows: int, k: int, phi=None) -> np.ndarray:
-    """Omega (complex128, [N, k]); with phi (length N) Omega_p = diag(phi) Omega."""
-    g = gaussian(seed, n_rows, k)
+def rademacher(seed: int, n_rows: int, k: int) -> np.ndarray:
+    """+-1 matrix [n_rows, k] (float64): -1 where bit 0 of the first word is set."""
+    w0 = raw_words(seed, n_rows, k)[0]
+    return np.where((w0 & np.uint32(1)) != 0, -1.0, 1.0)
+
+
+def sparse_threshold(density: float) -> int:
+    """Integer cut of the sparse Rademacher rule: entry kept iff w1 < this."""
+    if not (0.0 < density <= 1.0):
+        raise ValueError("density must be in (0, 1]")
+    return int(np.floor(density * 2.0 ** 32))
+
+
+def sparse_rademacher(seed: int, n_rows: int, k: int, density: float) -> np.ndarray:
+    """Sparse sign matrix: +-1/sqrt(d) with probability d, else 0."""
+    w0, w1 = raw_words(seed, n_rows, k)[:2]
+    keep = w1.astype(np.uint64) < np.uint64(sparse_threshold(density))
+    mag = 1.0 / np.sqrt(density)
+    sign = np.where((w0 & np.uint32(1)) != 0, -mag, mag)
+    return np.where(keep, sign, 0.0)
+
+
+KINDS = ("gaussian", "rademacher", "sparse_rademacher", "orthonormal")
+
+
+def test_matrix(seed: int, n_rows: int, k: int, phi=None, kind: str = "gaussian",
+                density: float = 1.0 / 3.0) -> np.ndarray:
+    """Omega (complex128, [N, k]); with phi (length N) Omega_p = diag(phi) Omega.
+
+    kind "orthonormal" returns diag(phi) G before its QR; resolvent.py takes
+    the QR (the orthonormalised test matrix of Sec. II.C)."""
+    if kind in ("gaussian", "orthonormal"):
+        g = gaussian(seed, n_rows, k)
+    elif kind == "rademacher":
+        g = rademacher(seed, n_rows, k)
+    elif kind == "sparse_rademacher":
+        g = sparse_rademacher(seed, n_rows, k, density)
+    else:
+        raise ValueError(f"unknown test matrix kind {kind!r}")
     if phi is not None:
         g = np.asarray(phi, dtype=np.float64)[:, None] * g
     return g.astype(np.complex128)

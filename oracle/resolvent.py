@@ -126,9 +126,19 @@ class RandResult:
     Q: np.ndarray            # orthonormal basis of Y [N, k]
 
 
+def _householder_q(A: np.ndarray) -> np.ndarray:
+    """Q of A = QR (Householder) with the diagonal of R made real positive,
+    which makes Q unique for full-rank A."""
+    Q, R = np.linalg.qr(A, mode="reduced")
+    d = np.diag(R)
+    ph = np.where(np.abs(d) > 0, d / np.where(np.abs(d) > 0, np.abs(d), 1.0), 1.0)
+    return Q * ph[None, :]
+
+
 def randomized(L: sp.spmatrix, s: complex, k: int, seed: int, phi=None,
                weights=None, orthogonalize: bool = False, method: str = "auto",
-               omega=None, lu=None) -> RandResult:
+               omega=None, lu=None, kind: str = "gaussian", density: float = 1.0 / 3.0,
+               power_iters: int = 0) -> RandResult:
     """Algorithm 1 (Sec. II.B) for the weighted resolvent at shift s.
 
     Steps, in the paper's order, with one factorisation of s I - L reused by
@@ -141,15 +151,28 @@ def randomized(L: sp.spmatrix, s: complex, k: int, seed: int, phi=None,
       U Sigma <- R V                     (solve, Eq. 8)
       sigma_j <- ||(U Sigma)_j||,  u_j <- (U Sigma)_j / sigma_j
       optionally (U, Sigma, Vt) <- svd(U Sigma), V <- V Vt
+
+    kind selects the test matrix of Sec. II.C (see philox.py); "orthonormal"
+    replaces Omega by the Q factor of diag(Phi) G.  power_iters = q > 0 runs
+    q subspace iterations (Sec. II.C; Halko, Martinsson & Tropp 2011,
+    Alg. 4.4) after the sketch, a QR between every two applications:
+      for each of q passes:  Z <- qr(R^H Q);  Q <- qr(R Z)
     """
     n = L.shape[0]
     wh = _weights(n, weights)
     if lu is None:
         lu = factor(op.shifted(L, s), method)
     if omega is None:
-        omega = philox.test_matrix(seed, n, k, phi)
+        omega = philox.test_matrix(seed, n, k, phi, kind=kind, density=density)
+        if kind == "orthonormal":
+            omega = _householder_q(omega)
     Y = wh[:, None] * lu.solve(omega / wh[:, None])
     Q, _ = np.linalg.qr(Y, mode="reduced")
+    for _ in range(power_iters):
+        Z = lu.solve_adjoint(Q * wh[:, None]) / wh[:, None]
+        Z, _ = np.linalg.qr(Z, mode="reduced")
+        Y = wh[:, None] * lu.solve(Z / wh[:, None])
+        Q, _ = np.linalg.qr(Y, mode="reduced")
     BH = lu.solve_adjoint(Q * wh[:, None]) / wh[:, None]
     Ub, Sb, Vh = np.linalg.svd(BH.conj().T, full_matrices=False)
     V = Vh.conj().T
