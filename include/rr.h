@@ -184,6 +184,45 @@ rr_status rr_sketch(rr_factors* f, int k, const uint64_t* seeds,
                     const double* phi, double refine_tol, int max_refine,
                     void* V, double* sigma_halko, rr_info* info);
 
+/* Test matrices of Sec. II.C, all drawn from one Philox-4x32-10 block per
+ * entry (key seeds[f], counter (n, j, 0, 0); words w0..w3):
+ *  RR_OMEGA_GAUSSIAN          Box-Muller N(0, 1) as described at rr_sketch;
+ *  RR_OMEGA_RADEMACHER        -1 if bit 0 of w0 is set, else +1;
+ *  RR_OMEGA_SPARSE_RADEMACHER nonzero iff w1 < floor(density * 2^32), then
+ *                             +-1/sqrt(density) with the Rademacher sign
+ *                             (mean 0, variance 1; density 1/3 is
+ *                             Achlioptas' sparse projection);
+ *  RR_OMEGA_ORTHONORMAL       the Q factor (CholeskyQR2, R with a real
+ *                             positive diagonal) of diag(phi) times the
+ *                             Gaussian matrix.
+ * Every kind is scaled by phi (Eq. 9) when phi is given. */
+typedef enum {
+  RR_OMEGA_GAUSSIAN = 0,
+  RR_OMEGA_RADEMACHER = 1,
+  RR_OMEGA_SPARSE_RADEMACHER = 2,
+  RR_OMEGA_ORTHONORMAL = 3
+} rr_omega_kind;
+
+/* Options of rr_sketch_ex.  power_iters = q runs q subspace iterations
+ * (Sec. II.C; Halko, Martinsson & Tropp 2011, Alg. 4.4) after the sketch:
+ * q times { Z = qr(R^H Q); Q = qr(R Z) }, every QR a CholeskyQR2, every
+ * solve reusing the factors (2k extra solves per iteration).  density is
+ * read only for RR_OMEGA_SPARSE_RADEMACHER. */
+typedef struct {
+  int omega_kind;   /* rr_omega_kind                       */
+  double density;   /* in (0, 1]                           */
+  int power_iters;  /* 0 .. 64                             */
+} rr_sketch_opts;
+
+/* rr_sketch with a choice of test matrix and subspace iterations.  opts NULL
+ * is rr_sketch (Gaussian, no iterations).  Errors as rr_sketch, plus
+ * RR_ERR_ARG for an unknown kind, a density outside (0, 1] or power_iters
+ * outside [0, 64]. */
+rr_status rr_sketch_ex(rr_factors* f, int k, const uint64_t* seeds,
+                       const double* phi, const rr_sketch_opts* opts,
+                       double refine_tol, int max_refine, void* V,
+                       double* sigma_halko, rr_info* info);
+
 /* Algorithm 1, last steps (Eq. 8): U Sigma = R V, sigma_j = ||(U Sigma)_j||,
  * u_j = (U Sigma)_j / sigma_j; with orthogonalize != 0 also the optional
  * SVD(U Sigma) = U Sigma Vt^H and V <- V Vt.  Results are sorted by sigma
@@ -200,6 +239,15 @@ rr_status rr_modes(rr_factors* f, int k, void* V, void* U, double* sigma,
  * host, nshift values; phi, omega: device (omega complex128 [F][N][k]). */
 rr_status rr_gaussian(int nshift, int n, int k, const uint64_t* seeds, const double* phi,
                       void* omega, void* stream);
+
+/* The test matrix alone for the Philox kinds (RR_OMEGA_GAUSSIAN,
+ * RR_OMEGA_RADEMACHER, RR_OMEGA_SPARSE_RADEMACHER; see rr_omega_kind):
+ * omega[f][n][j] = phi[n] * entry(seeds[f], n, j), imaginary parts zero.
+ * rr_gaussian is this call with RR_OMEGA_GAUSSIAN.  Errors: RR_ERR_ARG
+ * (null, sizes < 1, other kinds, density outside (0, 1]), RR_ERR_CUDA. */
+rr_status rr_test_matrix(int nshift, int n, int k, const uint64_t* seeds,
+                         const double* phi, int kind, double density,
+                         void* omega, void* stream);
 
 /* Re-factor an existing factors object for F new shifts (same operator,
  * count and precision), reusing its device storage: the per-frequency loop of

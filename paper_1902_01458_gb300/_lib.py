@@ -46,6 +46,14 @@ class rr_baseflow(ctypes.Structure):
                 ("v", ctypes.POINTER(ctypes.c_double))]
 
 
+class rr_sketch_opts(ctypes.Structure):
+    _fields_ = [("omega_kind", ctypes.c_int), ("density", ctypes.c_double),
+                ("power_iters", ctypes.c_int)]
+
+
+OMEGA_KINDS = {"gaussian": 0, "rademacher": 1, "sparse_rademacher": 2, "orthonormal": 3}
+
+
 class rr_info(ctypes.Structure):
     _fields_ = [("refine_iters", ctypes.c_int), ("refine_residual", ctypes.c_double),
                 ("cqr_cond", ctypes.c_double), ("cqr_shifted", ctypes.c_int),
@@ -77,6 +85,10 @@ SIGNATURES = {
     "rr_solve": (_I, [_P, _I, _I, _P, _P, _D, _I, ctypes.POINTER(rr_info)]),
     "rr_sketch": (_I, [_P, _I, ctypes.POINTER(ctypes.c_uint64), _P, _D, _I, _P, _P,
                        ctypes.POINTER(rr_info)]),
+    "rr_sketch_ex": (_I, [_P, _I, ctypes.POINTER(ctypes.c_uint64), _P,
+                          ctypes.POINTER(rr_sketch_opts), _D, _I, _P, _P,
+                          ctypes.POINTER(rr_info)]),
+    "rr_test_matrix": (_I, [_I, _I, _I, ctypes.POINTER(ctypes.c_uint64), _P, _I, _D, _P, _P]),
     "rr_modes": (_I, [_P, _I, _P, _P, _P, _I, _D, _I, ctypes.POINTER(rr_info)]),
     "rr_gaussian": (_I, [_I, _I, _I, ctypes.POINTER(ctypes.c_uint64), _P, _P, _P]),
     "rr_refactor": (_I, [_P, ctypes.POINTER(ctypes.c_double)]),
@@ -214,13 +226,21 @@ def rr_solve(h, b, x, adjoint=False, refine_tol=1e-10, max_refine=10):
     return st, info
 
 
-def rr_sketch(h, k, seeds, phi, V, sigma_halko, refine_tol=1e-10, max_refine=10):
+def rr_sketch(h, k, seeds, phi, V, sigma_halko, refine_tol=1e-10, max_refine=10,
+              omega_kind="gaussian", density=1.0 / 3.0, power_iters=0):
     info = rr_info()
     sd = np.asarray(seeds, dtype=np.uint64).ravel()
     arr = (ctypes.c_uint64 * sd.size)(*[int(x) for x in sd])
-    st = load().rr_sketch(h, int(k), arr, None if phi is None else _dptr(phi),
-                          float(refine_tol), int(max_refine), _dptr(V),
-                          _dptr(sigma_halko), ctypes.byref(info))
+    phip = None if phi is None else _dptr(phi)
+    if omega_kind == "gaussian" and power_iters == 0:
+        st = load().rr_sketch(h, int(k), arr, phip, float(refine_tol), int(max_refine),
+                              _dptr(V), _dptr(sigma_halko), ctypes.byref(info))
+    else:
+        kind = OMEGA_KINDS[omega_kind] if isinstance(omega_kind, str) else int(omega_kind)
+        opts = rr_sketch_opts(kind, float(density), int(power_iters))
+        st = load().rr_sketch_ex(h, int(k), arr, phip, ctypes.byref(opts), float(refine_tol),
+                                 int(max_refine), _dptr(V), _dptr(sigma_halko),
+                                 ctypes.byref(info))
     return st, info
 
 
@@ -259,6 +279,15 @@ def rr_gaussian(seeds, n, k, phi, omega, stream=None):
     _check(load().rr_gaussian(sd.size, int(n), int(k), arr,
                               None if phi is None else _dptr(phi), _dptr(omega),
                               _stream_ptr(stream)))
+
+
+def rr_test_matrix(seeds, n, k, phi, omega, kind="gaussian", density=1.0 / 3.0, stream=None):
+    sd = np.asarray(seeds, dtype=np.uint64).ravel()
+    arr = (ctypes.c_uint64 * sd.size)(*[int(x) for x in sd])
+    kind = OMEGA_KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(load().rr_test_matrix(sd.size, int(n), int(k), arr,
+                                 None if phi is None else _dptr(phi), kind, float(density),
+                                 _dptr(omega), _stream_ptr(stream)))
 
 
 # ---------------------------------------------------------- thin wrappers
@@ -347,11 +376,13 @@ class Factors:
             _check(st)
         return x, info.as_dict()
 
-    def sketch(self, k, seeds, phi=None, refine_tol=1e-10, max_refine=10):
+    def sketch(self, k, seeds, phi=None, refine_tol=1e-10, max_refine=10,
+               omega_kind="gaussian", density=1.0 / 3.0, power_iters=0):
         import torch
         V = torch.empty(self.F, self.op.n, k, dtype=torch.complex128, device=self._dev())
         sh = torch.empty(self.F, k, dtype=torch.float64, device=self._dev())
-        st, info = rr_sketch(self.handle, k, seeds, phi, V, sh, refine_tol, max_refine)
+        st, info = rr_sketch(self.handle, k, seeds, phi, V, sh, refine_tol, max_refine,
+                             omega_kind, density, power_iters)
         _check(st)
         return V, sh, info.as_dict()
 
@@ -366,9 +397,11 @@ class Factors:
         return U, sig, info.as_dict()
 
     def randomized_resolvent(self, k, seeds, phi=None, orthogonalize=False,
-                             refine_tol=1e-10, max_refine=10) -> ResolventResult:
+                             refine_tol=1e-10, max_refine=10, omega_kind="gaussian",
+                             density=1.0 / 3.0, power_iters=0) -> ResolventResult:
         """Algorithm 1 for every shift of the batch."""
-        V, sh, i1 = self.sketch(k, seeds, phi, refine_tol, max_refine)
+        V, sh, i1 = self.sketch(k, seeds, phi, refine_tol, max_refine, omega_kind, density,
+                                power_iters)
         U, sig, i2 = self.modes(V, orthogonalize, refine_tol, max_refine)
         info = {key: max(i1[key], i2[key]) for key in i1}
         return ResolventResult(sig, sh, U, V, info)

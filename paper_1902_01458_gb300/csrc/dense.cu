@@ -25,9 +25,14 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// Test-matrix entry (n, j) of problem f from one Philox-4x32-10 block with
+// key seeds[f], counter (n, j, 0, 0).  kind 0: Box-Muller normal from the
+// four words; kind 1: Rademacher sign, -1 iff bit 0 of w0 is set; kind 2:
+// sparse Rademacher, +-mag iff w1 < thresh (thresh = floor(d 2^32), mag =
+// 1/sqrt(d)), else 0.
 __global__ void philox_kernel(int F, int N, int k, const uint64_t* __restrict__ seeds,
                               const double* __restrict__ phi, const double* __restrict__ wis,
-                              double2* __restrict__ out) {
+                              double2* __restrict__ out, int kind, uint64_t thresh, double mag) {
   const size_t total = (size_t)F * N * k;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -39,11 +44,18 @@ __global__ void philox_kernel(int F, int N, int k, const uint64_t* __restrict__ 
     uint64_t s = seeds[f];
     uint4 w = philox4x32_10(make_uint4(n, j, 0u, 0u),
                             make_uint2((uint32_t)(s & 0xFFFFFFFFu), (uint32_t)(s >> 32)));
-    uint64_t m1 = ((uint64_t)(w.x >> 5) << 26) + (w.y >> 6);
-    uint64_t m2 = ((uint64_t)(w.z >> 5) << 26) + (w.w >> 6);
-    double u1 = ((double)m1 + 1.0) * 0x1p-53;
-    double u2 = (double)m2 * 0x1p-53;
-    double g = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
+    double g;
+    if (kind == 0) {
+      uint64_t m1 = ((uint64_t)(w.x >> 5) << 26) + (w.y >> 6);
+      uint64_t m2 = ((uint64_t)(w.z >> 5) << 26) + (w.w >> 6);
+      double u1 = ((double)m1 + 1.0) * 0x1p-53;
+      double u2 = (double)m2 * 0x1p-53;
+      g = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
+    } else if (kind == 1) {
+      g = (w.x & 1u) ? -1.0 : 1.0;
+    } else {
+      g = ((uint64_t)w.y < thresh) ? ((w.x & 1u) ? -mag : mag) : 0.0;
+    }
     if (phi) g *= phi[n];
     if (wis) g *= wis[n];
     out[e] = make_double2(g, 0.0);
@@ -479,9 +491,17 @@ int grid1d(size_t total, int threads) {
 }  // namespace
 
 rr_status launch_philox(int F, int N, int k, const uint64_t* seeds, const double* phi,
-                        const double* wis, double2* out, cudaStream_t st) {
+                        const double* wis, double2* out, cudaStream_t st, int kind,
+                        double density) {
+  uint64_t thresh = 0;
+  double mag = 1.0;
+  if (kind == 2) {
+    thresh = (uint64_t)std::floor(density * 4294967296.0);
+    mag = 1.0 / std::sqrt(density);
+  }
   prof_count(1);
-  philox_kernel<<<grid1d((size_t)F * N * k, 256), 256, 0, st>>>(F, N, k, seeds, phi, wis, out);
+  philox_kernel<<<grid1d((size_t)F * N * k, 256), 256, 0, st>>>(F, N, k, seeds, phi, wis, out,
+                                                                 kind, thresh, mag);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }

@@ -619,13 +619,27 @@ extern "C" rr_status rr_solve(rr_factors* fa, int k, int adjoint, const void* b,
   return s;
 }
 
-extern "C" rr_status rr_sketch(rr_factors* fa, int k, const uint64_t* seeds, const double* phi,
-                               double refine_tol, int max_refine, void* V, double* sigma_halko,
-                               rr_info* info) {
+static rr_status check_opts(const rr_sketch_opts* o, const char* who) {
+  if (!o) return RR_OK;
+  if (o->omega_kind < RR_OMEGA_GAUSSIAN || o->omega_kind > RR_OMEGA_ORTHONORMAL)
+    return arg_error(std::string(who) + ": unknown omega_kind");
+  if (o->omega_kind == RR_OMEGA_SPARSE_RADEMACHER && !(o->density > 0.0 && o->density <= 1.0))
+    return arg_error(std::string(who) + ": density must be in (0, 1]");
+  if (o->power_iters < 0 || o->power_iters > 64)
+    return arg_error(std::string(who) + ": power_iters must be in [0, 64]");
+  return RR_OK;
+}
+
+extern "C" rr_status rr_sketch_ex(rr_factors* fa, int k, const uint64_t* seeds, const double* phi,
+                                  const rr_sketch_opts* opts, double refine_tol, int max_refine,
+                                  void* V, double* sigma_halko, rr_info* info) {
   rr_status s = check_k(fa, k, "rr_sketch");
   if (s != RR_OK) return s;
   if (!seeds || !V || !sigma_halko) return arg_error("rr_sketch: null argument");
   if (max_refine < 0) return arg_error("rr_sketch: max_refine must be >= 0");
+  if ((s = check_opts(opts, "rr_sketch")) != RR_OK) return s;
+  const int kind = opts ? opts->omega_kind : RR_OMEGA_GAUSSIAN;
+  const int power_iters = opts ? opts->power_iters : 0;
   DeviceGuard guard(fa->op->d.device);
   info_reset(info);
   Work w;
@@ -635,20 +649,48 @@ extern "C" rr_status rr_sketch(rr_factors* fa, int k, const uint64_t* seeds, con
   const size_t bytes = (size_t)F * N * k * sizeof(double2);
   cudaStream_t st = fa->stream;
   rr_status conv = RR_OK;
+  auto note = [&](rr_status r) {
+    if (r == RR_ERR_NOCONV) conv = r;
+    return r == RR_ERR_NOCONV ? RR_OK : r;
+  };
   RR_CUDA(cudaMemcpyAsync(w.seeds, seeds, F * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-  // Omega' = W^{-1/2} diag(phi) randn  (first step, Eq. 9)
-  if ((s = launch_philox(F, N, k, w.seeds, phi, d.wisqrt, w.W1, st)) != RR_OK) return s;
+  // Omega' = W^{-1/2} diag(phi) Omega  (first step, Eq. 9)
+  if (kind == RR_OMEGA_ORTHONORMAL) {
+    // Omega = Q factor of diag(phi) randn (CholeskyQR2), then weighted
+    if ((s = launch_philox(F, N, k, w.seeds, phi, nullptr, w.W1, st, 0)) != RR_OK) return s;
+    if ((s = cholqr2(fa, k, w.W1, nullptr, w, info)) != RR_OK) return s;
+    if ((s = launch_scale_rows(F, N, k, d.wisqrt, w.W1, st)) != RR_OK) return s;
+  } else {
+    const double dens = opts ? opts->density : 1.0;
+    if ((s = launch_philox(F, N, k, w.seeds, phi, d.wisqrt, w.W1, st, kind, dens)) != RR_OK)
+      return s;
+  }
   // Y = W^{1/2} A^{-1} Omega'  (second step)
-  s = solve_refined(fa, k, 0, w.W1, w.W2, refine_tol, max_refine, w, info);
-  if (s == RR_ERR_NOCONV) conv = s; else if (s != RR_OK) return s;
+  if ((s = note(solve_refined(fa, k, 0, w.W1, w.W2, refine_tol, max_refine, w, info))) != RR_OK)
+    return s;
   if ((s = launch_scale_rows(F, N, k, d.wsqrt, w.W2, st)) != RR_OK) return s;
   // Q = qr(Y)  (third step)
   if ((s = cholqr2(fa, k, w.W2, nullptr, w, info)) != RR_OK) return s;
+  // subspace iterations: Z = qr(R^H Q), Q = qr(R Z)
+  for (int it = 0; it < power_iters; ++it) {
+    RR_CUDA(cudaMemcpyAsync(w.W1, w.W2, bytes, cudaMemcpyDeviceToDevice, st));
+    if ((s = launch_scale_rows(F, N, k, d.wsqrt, w.W1, st)) != RR_OK) return s;
+    if ((s = note(solve_refined(fa, k, 1, w.W1, w.W3, refine_tol, max_refine, w, info))) != RR_OK)
+      return s;
+    if ((s = launch_scale_rows(F, N, k, d.wisqrt, w.W3, st)) != RR_OK) return s;
+    if ((s = cholqr2(fa, k, w.W3, nullptr, w, info)) != RR_OK) return s;
+    RR_CUDA(cudaMemcpyAsync(w.W1, w.W3, bytes, cudaMemcpyDeviceToDevice, st));
+    if ((s = launch_scale_rows(F, N, k, d.wisqrt, w.W1, st)) != RR_OK) return s;
+    if ((s = note(solve_refined(fa, k, 0, w.W1, w.W2, refine_tol, max_refine, w, info))) != RR_OK)
+      return s;
+    if ((s = launch_scale_rows(F, N, k, d.wsqrt, w.W2, st)) != RR_OK) return s;
+    if ((s = cholqr2(fa, k, w.W2, nullptr, w, info)) != RR_OK) return s;
+  }
   // B^H = W^{-1/2} A^{-H} W^{1/2} Q  (fourth step)
   RR_CUDA(cudaMemcpyAsync(w.W1, w.W2, bytes, cudaMemcpyDeviceToDevice, st));
   if ((s = launch_scale_rows(F, N, k, d.wsqrt, w.W1, st)) != RR_OK) return s;
-  s = solve_refined(fa, k, 1, w.W1, w.W3, refine_tol, max_refine, w, info);
-  if (s == RR_ERR_NOCONV) conv = s; else if (s != RR_OK) return s;
+  if ((s = note(solve_refined(fa, k, 1, w.W1, w.W3, refine_tol, max_refine, w, info))) != RR_OK)
+    return s;
   if ((s = launch_scale_rows(F, N, k, d.wisqrt, w.W3, st)) != RR_OK) return s;
   // svd(B): B^H = Q_B R_B, R_B = Ul S Vr^H  =>  V = Q_B Ul, sigma = S  (fifth step)
   if ((s = cholqr2(fa, k, w.W3, w.R2i, w, info)) != RR_OK) return s;
@@ -657,6 +699,12 @@ extern "C" rr_status rr_sketch(rr_factors* fa, int k, const uint64_t* seeds, con
   RR_CUDA(cudaMemcpyAsync(sigma_halko, w.sig, (size_t)F * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
   RR_CUDA(cudaStreamSynchronize(st));
   return conv;
+}
+
+extern "C" rr_status rr_sketch(rr_factors* fa, int k, const uint64_t* seeds, const double* phi,
+                               double refine_tol, int max_refine, void* V, double* sigma_halko,
+                               rr_info* info) {
+  return rr_sketch_ex(fa, k, seeds, phi, nullptr, refine_tol, max_refine, V, sigma_halko, info);
 }
 
 extern "C" rr_status rr_modes(rr_factors* fa, int k, void* V, void* U, double* sigma,
@@ -730,16 +778,27 @@ extern "C" rr_status rr_refactor(rr_factors* fa, const double* shifts) {
 
 extern "C" rr_status rr_gaussian(int nshift, int n, int k, const uint64_t* seeds, const double* phi,
                                  void* omega, void* stream) {
-  if (!seeds || !omega) return arg_error("rr_gaussian: null argument");
-  if (nshift < 1 || n < 1 || k < 1) return arg_error("rr_gaussian: sizes must be >= 1");
+  return rr_test_matrix(nshift, n, k, seeds, phi, RR_OMEGA_GAUSSIAN, 1.0, omega, stream);
+}
+
+extern "C" rr_status rr_test_matrix(int nshift, int n, int k, const uint64_t* seeds,
+                                    const double* phi, int kind, double density, void* omega,
+                                    void* stream) {
+  if (!seeds || !omega) return arg_error("rr_test_matrix: null argument");
+  if (nshift < 1 || n < 1 || k < 1) return arg_error("rr_test_matrix: sizes must be >= 1");
+  if (kind < RR_OMEGA_GAUSSIAN || kind > RR_OMEGA_SPARSE_RADEMACHER)
+    return arg_error("rr_test_matrix: kind must be Gaussian, Rademacher or sparse Rademacher");
+  if (kind == RR_OMEGA_SPARSE_RADEMACHER && !(density > 0.0 && density <= 1.0))
+    return arg_error("rr_test_matrix: density must be in (0, 1]");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   uint64_t* sd = nullptr;
   rr_status s = dalloc(&sd, nshift * sizeof(uint64_t));
   if (s != RR_OK) return s;
   cudaError_t e = cudaMemcpyAsync(sd, seeds, nshift * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) s = launch_philox(nshift, n, k, sd, phi, nullptr, (double2*)omega, st);
+  if (e == cudaSuccess)
+    s = launch_philox(nshift, n, k, sd, phi, nullptr, (double2*)omega, st, kind, density);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(sd);
-  if (e != cudaSuccess) return cuda_status(e, "rr_gaussian");
+  if (e != cudaSuccess) return cuda_status(e, "rr_test_matrix");
   return s;
 }

@@ -160,8 +160,10 @@ int factor_panel_width(int prec, int b);
 rr_status launch_solve_lo(rr_factors* f, int k, int adjoint, const void* b, void* x, void* tmp);
 
 // dense.cu
+// kind: 0 Gaussian, 1 Rademacher, 2 sparse Rademacher of the given density
 rr_status launch_philox(int F, int N, int k, const uint64_t* seeds_dev, const double* phi,
-                        const double* wisqrt, double2* out, cudaStream_t st);
+                        const double* wisqrt, double2* out, cudaStream_t st, int kind = 0,
+                        double density = 1.0);
 rr_status launch_scale_rows(int F, int N, int k, const double* w, double2* x, cudaStream_t st);
 rr_status launch_convert_d2f(size_t n, const double2* in, float2* out, cudaStream_t st);
 rr_status launch_convert_f2d(size_t n, const float2* in, double2* out, int accumulate,
