@@ -249,6 +249,30 @@ rr_status rr_test_matrix(int nshift, int n, int k, const uint64_t* seeds,
                          const double* phi, int kind, double density,
                          void* omega, void* stream);
 
+/* Gradient of the summed leading gains with respect to the base flow (no
+ * counterpart in the paper; it differentiates Eq. 5):
+ *
+ *   grad += d/d(rho, U, V) sum_f sum_{j<J} sigma_{f,j}^2
+ *         = sum_f sum_{j<J} 2 sigma_j Re(a_j^H (dL/dtheta) b_j),
+ *   a_j = A^{-H} W^{1/2} u_j,  b_j = A^{-1} W^{-1/2} v_j,  A = s_f I - L,
+ *
+ * the first-order perturbation of a simple singular value with singular
+ * vectors u_j, v_j (d sigma_j = Re(u_j^H dR v_j)).  The 2J solves reuse the
+ * factors (with FP64 refinement for FP32 factors); dL/dtheta is the exact
+ * derivative of the discrete operator of rr_create_operator with respect to
+ * the nodal base-flow values, the base flow the operator was built from.
+ * U, V: device [F][N][k] with unit columns (as returned by rr_modes), of
+ * which the first J are used; sigma: device [F][k]; grad: device, 3*nx*ny
+ * doubles laid out [rho | U | V], each field point-indexed ix*ny + iy,
+ * ACCUMULATED into (zero it first; the rho part stays untouched for
+ * RR_ADVDIFF_SCALAR).  The result is the gradient of the true leading gains
+ * to the accuracy of the given triplets: exact triplets give the exact
+ * gradient.  Errors: RR_ERR_ARG (J outside [1, k], k outside [1, 64], null),
+ * RR_ERR_NOCONV (grad still accumulated), RR_ERR_CUDA. */
+rr_status rr_gain_grad(rr_factors* f, int k, int J, const void* U, const void* V,
+                       const double* sigma, double refine_tol, int max_refine,
+                       double* grad, rr_info* info);
+
 /* Re-factor an existing factors object for F new shifts (same operator,
  * count and precision), reusing its device storage: the per-frequency loop of
  * a frequency sweep without reallocation.  Errors as rr_factor. */

@@ -92,6 +92,7 @@ SIGNATURES = {
     "rr_modes": (_I, [_P, _I, _P, _P, _P, _I, _D, _I, ctypes.POINTER(rr_info)]),
     "rr_gaussian": (_I, [_I, _I, _I, ctypes.POINTER(ctypes.c_uint64), _P, _P, _P]),
     "rr_refactor": (_I, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "rr_gain_grad": (_I, [_P, _I, _I, _P, _P, _P, _D, _I, _P, ctypes.POINTER(rr_info)]),
     "rr_launch_count": (ctypes.c_longlong, []),
     "rr_profile_start": (_I, [ctypes.c_uint]),
     "rr_profile_read": (_I, [_I, ctypes.POINTER(ctypes.c_double),
@@ -251,6 +252,15 @@ def rr_modes(h, k, V, U, sigma, orthogonalize=False, refine_tol=1e-10, max_refin
     return st, info
 
 
+def rr_gain_grad(h, J, U, V, sigma, grad, refine_tol=1e-10, max_refine=10):
+    info = rr_info()
+    k = U.shape[2]
+    st = load().rr_gain_grad(h, int(k), int(J), _dptr(U), _dptr(V), _dptr(sigma),
+                             float(refine_tol), int(max_refine), _dptr(grad),
+                             ctypes.byref(info))
+    return st, info
+
+
 def rr_refactor(h, shifts):
     _check(load().rr_refactor(h, _shift_array(shifts)))
 
@@ -395,6 +405,17 @@ class Factors:
                             max_refine)
         _check(st)
         return U, sig, info.as_dict()
+
+    def gain_grad(self, J, U, V, sigma, grad=None, refine_tol=1e-10, max_refine=10):
+        """grad += d(sum over shifts of sum_{j<J} sigma_j^2)/d(rho, U, V), shape
+        [3, nx, ny] float64 on the device (allocated zeroed when None)."""
+        import torch
+        if grad is None:
+            grad = torch.zeros(3, self.op.nx, self.op.ny, dtype=torch.float64,
+                               device=self._dev())
+        st, info = rr_gain_grad(self.handle, J, U, V, sigma, grad, refine_tol, max_refine)
+        _check(st)
+        return grad, info.as_dict()
 
     def randomized_resolvent(self, k, seeds, phi=None, orthogonalize=False,
                              refine_tol=1e-10, max_refine=10, omega_kind="gaussian",

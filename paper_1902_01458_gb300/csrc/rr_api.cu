@@ -99,6 +99,7 @@ struct Work {
   int *bad, *rank, *sweeps;
   double2* phase;
   uint64_t* seeds;
+  double* featbar;              // [nx*ny][18] gradient scratch
   int nblk_gram, nblk_col;
 };
 
@@ -145,6 +146,7 @@ size_t carve(rr_factors* fa, int k, char* base, Work* w) {
   t.sweeps = (int*)take((size_t)F * sizeof(int));
   t.phase = (double2*)take((size_t)F * k * sizeof(double2));
   t.seeds = (uint64_t*)take((size_t)F * sizeof(uint64_t));
+  t.featbar = (double*)take((size_t)fa->op->d.nx * fa->op->d.ny * 18 * sizeof(double));
   t.nblk_gram = nblk_gram;
   t.nblk_col = nblk_col;
   if (w) *w = t;
@@ -742,6 +744,43 @@ extern "C" rr_status rr_modes(rr_factors* fa, int k, void* V, void* U, double* s
   }
   if ((s = launch_finish_modes(F, N, k, (double2*)U, (double2*)V, sigma, w.W1, w.W3, w.dpart,
                                w.nblk_col, w.rank, w.phase, st)) != RR_OK)
+    return s;
+  RR_CUDA(cudaStreamSynchronize(st));
+  return conv;
+}
+
+extern "C" rr_status rr_gain_grad(rr_factors* fa, int k, int J, const void* U, const void* V,
+                                  const double* sigma, double refine_tol, int max_refine,
+                                  double* grad, rr_info* info) {
+  rr_status s = check_k(fa, k, "rr_gain_grad");
+  if (s != RR_OK) return s;
+  if (!U || !V || !sigma || !grad) return arg_error("rr_gain_grad: null argument");
+  if (J < 1 || J > k) return arg_error("rr_gain_grad: J must be in [1, k]");
+  if (max_refine < 0) return arg_error("rr_gain_grad: max_refine must be >= 0");
+  DeviceGuard guard(fa->op->d.device);
+  info_reset(info);
+  Work w;
+  if ((s = get_work(fa, J, &w)) != RR_OK) return s;
+  const OpDev& d = fa->op->d;
+  const int F = fa->F, N = d.n;
+  cudaStream_t st = fa->stream;
+  rr_status conv = RR_OK;
+  // first J columns of U and V: [F][N][k] -> [F][N][J]
+  const size_t rows = (size_t)F * N;
+  // a_j = A^{-H} W^{1/2} u_j
+  RR_CUDA(cudaMemcpy2DAsync(w.W1, J * sizeof(double2), U, k * sizeof(double2),
+                            J * sizeof(double2), rows, cudaMemcpyDeviceToDevice, st));
+  if ((s = launch_scale_rows(F, N, J, d.wsqrt, w.W1, st)) != RR_OK) return s;
+  s = solve_refined(fa, J, 1, w.W1, w.W2, refine_tol, max_refine, w, info);
+  if (s == RR_ERR_NOCONV) conv = s; else if (s != RR_OK) return s;
+  // b_j = A^{-1} W^{-1/2} v_j
+  RR_CUDA(cudaMemcpy2DAsync(w.W1, J * sizeof(double2), V, k * sizeof(double2),
+                            J * sizeof(double2), rows, cudaMemcpyDeviceToDevice, st));
+  if ((s = launch_scale_rows(F, N, J, d.wisqrt, w.W1, st)) != RR_OK) return s;
+  s = solve_refined(fa, J, 0, w.W1, w.W3, refine_tol, max_refine, w, info);
+  if (s == RR_ERR_NOCONV) conv = s; else if (s != RR_OK) return s;
+  if ((s = launch_gain_grad(d, fa->op->grid, F, J, w.W2, w.W3, sigma, k, w.featbar, grad, st)) !=
+      RR_OK)
     return s;
   RR_CUDA(cudaStreamSynchronize(st));
   return conv;

@@ -188,6 +188,13 @@ rr_status launch_finish_modes(int F, int N, int k, double2* U, double2* V, doubl
 
 rr_status launch_axpy(size_t n, const double2* d, double2* x, cudaStream_t st);
 
+// grad.cu: grad[3][nx*ny] += d(sum_f sum_{j<J} sigma_j^2)/d(rho, U, V) from the
+// sandwich vectors A = A^{-H} W^{1/2} u, B = A^{-1} W^{-1/2} v ([F][N][J]);
+// sigma [F][sstride]; featbar scratch [nx*ny][18].
+rr_status launch_gain_grad(const OpDev& d, const rr_grid& g, int F, int J, const double2* A,
+                           const double2* B, const double* sigma, int sstride, double* featbar,
+                           double* grad, cudaStream_t st);
+
 // prof.cu: launch counting and per-class event timing (classes of rr.h)
 enum {
   PROF_SCHUR = 0, PROF_PANEL = 1, PROF_ROWBLOCK = 2, PROF_UPDATE = 3, PROF_FINALIZE = 4,
