@@ -137,11 +137,22 @@ __global__ void gram_part_kernel(int N, int k, int nblk, const double2* __restri
   const int rows_per = (N + nblk - 1) / nblk;
   const int n0 = blk * rows_per, n1 = min(N, n0 + rows_per);
   const double2* Yf = Y + (size_t)f * N * k;
-  const int kk = k * k;
-  double2 acc[16];
-  const int npair = (kk + blockDim.x - 1) / blockDim.x;  // <= 16 for k <= 64
+  // G is Hermitian: only the pairs a <= c (k (k+1)/2 of them) are formed
+  const int kk = k * k, nup = k * (k + 1) / 2;
+  double2 acc[9];
+  int pa[9], pc[9];
+  const int npair = (nup + blockDim.x - 1) / blockDim.x;  // <= 9 for k <= 64
 #pragma unroll
-  for (int t = 0; t < 16; ++t) acc[t] = make_double2(0.0, 0.0);
+  for (int t = 0; t < 9; ++t) {
+    acc[t] = make_double2(0.0, 0.0);
+    int rem = threadIdx.x + t * blockDim.x, a = 0;
+    while (a < k && rem >= k - a) {
+      rem -= k - a;
+      ++a;
+    }
+    pa[t] = a;
+    pc[t] = a + rem;
+  }
   for (int nb = n0; nb < n1; nb += GRAM_ROWS) {
     const int rows = min(GRAM_ROWS, n1 - nb);
     for (int e = threadIdx.x; e < GRAM_ROWS * k; e += blockDim.x) {
@@ -150,20 +161,20 @@ __global__ void gram_part_kernel(int N, int k, int nblk, const double2* __restri
     }
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
+    for (int t = 0; t < 9; ++t) {
       if (t >= npair) break;
-      int p = threadIdx.x + t * blockDim.x;
-      if (p >= kk) break;
-      int a = p / k, c = p - a * k;
+      if (threadIdx.x + t * blockDim.x >= nup) break;
+      const int a = pa[t], c = pc[t];
       double2 s = acc[t];
       for (int r = 0; r < rows; ++r) s = cfmac(Ys[r * k + a], Ys[r * k + c], s);
       acc[t] = s;
     }
     __syncthreads();
   }
-  for (int t = 0; t < npair; ++t) {
-    int p = threadIdx.x + t * blockDim.x;
-    if (p < kk) part[((size_t)f * nblk + blk) * kk + p] = acc[t];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    if (t >= npair || threadIdx.x + t * blockDim.x >= nup) break;
+    part[((size_t)f * nblk + blk) * kk + pa[t] * k + pc[t]] = acc[t];
   }
 }
 
@@ -173,8 +184,12 @@ __global__ void gram_reduce_kernel(int F, int k, int nblk, const double2* __rest
   int kk = k * k;
   if (e >= F * kk) return;
   int f = e / kk, p = e % kk;
+  const int a = p / k, c = p - a * k;
+  // only the upper triangle was formed: G[c][a] = conj(G[a][c])
+  const int src = a <= c ? p : c * k + a;
   double2 s = make_double2(0.0, 0.0);
-  for (int b = 0; b < nblk; ++b) s = cadd(s, part[((size_t)f * nblk + b) * kk + p]);
+  for (int b = 0; b < nblk; ++b) s = cadd(s, part[((size_t)f * nblk + b) * kk + src]);
+  if (a > c) s.y = -s.y;
   G[e] = s;
 }
 
@@ -257,6 +272,7 @@ __global__ void cholesky_kernel(int k, const double2* __restrict__ Gall, double2
 }
 
 // out[f][n][:] = Y[f][n][:] . S[f] (k x k); in place allowed (rows staged).
+// out = Y S per problem (S k x k row-major).
 __global__ void right_mul_kernel(int N, int k, int RB, const double2* Y,
                                  const double2* __restrict__ Sall, double2* out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -16,9 +16,13 @@
 //              M[K,R] <- T^{-1} B
 //   update   : M[I,R] <- M[I,R] + M[I,K] B    (= D - C A^{-1} B)
 // After the last panel M = (P S)^{-1}; S^{-1} is M with its columns permuted.
+#include <cuda.h>
+
 #include <algorithm>
+#include <type_traits>
 
 #include "rr_internal.cuh"
+#include "tc.cuh"
 
 namespace {
 
@@ -423,6 +427,277 @@ gj_update_kernel(int b, int k0, int nbk, int c_begin, int c_end, int ex_lo, int 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Trailing update on the tensor cores (FP32 factors, 32-column panels):
+// M[I,R] += M[I,K] B as a real GEMM on tcgen05.mma kind::tf32.
+//
+// A tile is 128 rows of M[., K] read interleaved (re, im) as 64 K-major reals;
+// the right operand is B expanded to B~ with rows (Re, -Im), (Im, Re) per
+// complex column, so one real product gives the complex one.  FP32 accuracy
+// comes from the 3xTF32 split (hi.hi + hi.lo + lo.hi into one FP32 TMEM
+// accumulator).  One CTA per item (problem, tile of 64 complex columns): it
+// expands B~ once and streams the row tiles of M through a warp-specialised
+// pipeline:
+//   warp 10     loads the raw A tile of row tile t+1 by TMA (3-D map over M)
+//               and issues the 24 MMAs of tile t into accumulator t & 1,
+//   warps 8-9   split the raw A tile into the hi / lo operand tiles,
+//   warps 0-7   prefetch the M rows of tile t (coalesced, whole 512-byte tile
+//               rows per warp instruction), move accumulator t & 1 through a
+//               shared staging tile and add it to M in place (rows in K,
+//               columns in K and in [ex_lo, ex_hi) untouched),
+// so the HBM traffic of tile t overlaps the split and MMAs of tile t+1.
+// Every mbarrier wait is bounded; a timeout sets *err and the CTA winds down
+// (in-flight MMAs drain, TMEM is freed).
+constexpr int UTC_RT = 128;                                   // rows per tile
+constexpr int UTC_CT = 64;                                    // complex columns per tile
+constexpr uint32_t UTC_LBO = 128, UTC_SBO = 2048;             // 64 reals of K
+constexpr uint32_t UTC_OP_BYTES = UTC_RT * 64 * 4;            // 32 KB operand tile
+constexpr int UTC_STAGE_LD = 2 * UTC_CT + 4;                  // staging row pitch (floats)
+constexpr uint32_t UTC_STAGE_BYTES = UTC_RT * UTC_STAGE_LD * 4;
+constexpr int UTC_EPI = 256, UTC_CONV = 64;                   // epilogue / split threads
+constexpr int UTC_THREADS = UTC_EPI + UTC_CONV + 32;          // + MMA warp
+// B~ hi/lo, A hi/lo, the raw A tile (TMA destination) and the staging tile
+constexpr size_t UTC_SMEM = 5 * (size_t)UTC_OP_BYTES + UTC_STAGE_BYTES + 128;
+constexpr uint32_t UTC_WAIT_TRIES = 1u << 22;
+
+// bounded wait; gives up at once when another thread has aborted
+__device__ __forceinline__ bool utc_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t t = 0; t < UTC_WAIT_TRIES; ++t) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void utc_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// barrier among the 256 epilogue threads only
+__device__ __forceinline__ void utc_epi_sync() {
+  asm volatile("bar.sync 1, %0;\n" ::"n"(UTC_EPI) : "memory");
+}
+
+__global__ void __launch_bounds__(UTC_THREADS, 1)
+gj_update_tc_kernel(const __grid_constant__ CUtensorMap tmapM, int b, int k0, int nbk, int c_begin,
+                    int c_end, int ex_lo, int ex_hi, float2* __restrict__ Mall,
+                    const float2* __restrict__ Ball, int F, int nct, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t raw_full, a_full, mma_done[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_sh;
+  volatile int* abort_flag = &abort_sh;
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  unsigned char* Bhi = base;
+  unsigned char* Blo = base + UTC_OP_BYTES;
+  unsigned char* Ahi = base + 2 * UTC_OP_BYTES;
+  unsigned char* Alo = base + 3 * UTC_OP_BYTES;
+  const float* Araw = reinterpret_cast<const float*>(base + 4 * UTC_OP_BYTES);  // [128][64]
+  float* stage = reinterpret_cast<float*>(base + 5 * UTC_OP_BYTES);  // [128][UTC_STAGE_LD]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool is_epi = tid < UTC_EPI;
+  const bool is_conv = tid >= UTC_EPI && tid < UTC_EPI + UTC_CONV;
+  const bool is_mma = tid == UTC_EPI + UTC_CONV;
+  const int nrt = (b + UTC_RT - 1) / UTC_RT;
+  const int nitems = nct * F;
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
+  if (tid == 0) {
+    tc::mbar_init(&raw_full, 1);
+    tc::mbar_init(&a_full, UTC_CONV);
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&mma_done[q], 1);
+      tc::mbar_init(&acc_empty[q], UTC_EPI);
+    }
+    abort_sh = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = tc::idesc_tf32(UTC_RT, 2 * UTC_CT);
+  uint64_t dBhi = 0, dBlo = 0, dAhi = 0, dAlo = 0;
+  if (is_mma) {
+    dBhi = tc::smem_desc(tc::smem_u32(Bhi), UTC_LBO, UTC_SBO);
+    dBlo = tc::smem_desc(tc::smem_u32(Blo), UTC_LBO, UTC_SBO);
+    dAhi = tc::smem_desc(tc::smem_u32(Ahi), UTC_LBO, UTC_SBO);
+    dAlo = tc::smem_desc(tc::smem_u32(Alo), UTC_LBO, UTC_SBO);
+  }
+  int g = 0;           // row tiles of this CTA so far (all items)
+  int issued = 0;      // tiles whose MMAs were issued (MMA thread)
+  int tma_issued = 0;  // raw A tiles requested (MMA thread)
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int f = it / nct, ct = it - f * nct;
+    const int c0 = c_begin + ct * UTC_CT;
+    float2* M = Mall + (size_t)f * b * b;
+    // every earlier tile's MMAs are complete here (their epilogues waited
+    // for them before this barrier), so B~ may be overwritten
+    __syncthreads();
+    if ((is_epi || is_conv) && !*abort_flag) {
+      const float2* B = Ball + (size_t)f * 32 * b;
+      for (int e = tid; e < UTC_CT * 16; e += UTC_EPI + UTC_CONV) {
+        const int j = e & (UTC_CT - 1), p = e / UTC_CT;
+        const int c = c0 + j, m0 = 2 * p, m1 = m0 + 1;
+        const bool cv = c < c_end;
+        const float2 t0 = (cv && m0 < nbk) ? B[(size_t)m0 * b + c] : make_float2(0.f, 0.f);
+        const float2 t1 = (cv && m1 < nbk) ? B[(size_t)m1 * b + c] : make_float2(0.f, 0.f);
+        float4 h0, l0;
+        tc::split_tf32(t0.x, h0.x, l0.x);
+        tc::split_tf32(-t0.y, h0.y, l0.y);
+        tc::split_tf32(t1.x, h0.z, l0.z);
+        tc::split_tf32(-t1.y, h0.w, l0.w);
+        const float4 h1 = make_float4(-h0.y, h0.x, -h0.w, h0.z);
+        const float4 l1 = make_float4(-l0.y, l0.x, -l0.w, l0.z);
+        const int n0 = 2 * j, n1 = n0 + 1;
+        const uint32_t o0 = (uint32_t)(n0 >> 3) * UTC_SBO + (uint32_t)p * UTC_LBO + (uint32_t)(n0 & 7) * 16;
+        const uint32_t o1 = (uint32_t)(n1 >> 3) * UTC_SBO + (uint32_t)p * UTC_LBO + (uint32_t)(n1 & 7) * 16;
+        *reinterpret_cast<float4*>(Bhi + o0) = h0;
+        *reinterpret_cast<float4*>(Blo + o0) = l0;
+        *reinterpret_cast<float4*>(Bhi + o1) = h1;
+        *reinterpret_cast<float4*>(Blo + o1) = l1;
+      }
+      tc::fence_async_smem();
+    }
+    __syncthreads();
+    if (is_mma && !*abort_flag) {  // raw A tile of the item's first row tile
+      tc::mbar_expect_tx(&raw_full, UTC_OP_BYTES);
+      tc::tma_load_3d(base + 4 * UTC_OP_BYTES, &tmapM, 2 * k0, 0, f, &raw_full);
+      ++tma_issued;
+    }
+    for (int rt = 0; rt < nrt; ++rt, ++g) {
+      const int q = g & 1;
+      const uint32_t ph = (uint32_t)(g >> 1) & 1u;  // phase of tile g on the barriers q
+      if (is_conv) {
+        // raw A tile (row-major 128 x 64 floats: rows rt*128.., the 32 panel
+        // columns; zero beyond b) -> TF32 hi / lo tiles in the K-major
+        // core-matrix layout.  Each 8-lane phase takes a diagonal: rows
+        // 8G + a and K groups ((a + D) & 7) + 8H for a = 0..7, so both the
+        // raw reads (slot p mod 8) and the core-matrix writes (slot i mod 8)
+        // hit 8 distinct 16-byte bank slots.
+        const int ci = tid - UTC_EPI;
+        bool ok = !*abort_flag;
+        if (ok) ok = utc_wait(&raw_full, (uint32_t)g & 1u, abort_flag);
+        // the A operand tiles are free once tile g-1's MMAs are complete
+        if (ok && g >= 1) ok = utc_wait(&mma_done[(g - 1) & 1], (uint32_t)((g - 1) >> 1) & 1u, abort_flag);
+        if (ok) {
+#pragma unroll 8
+          for (int s = 0; s < 32; ++s) {
+            const int a = lane & 7;
+            const int combo = ((ci >> 5) * 32 + s) * 4 + (lane >> 3);  // 0 .. 255
+            const int i = 8 * (combo & 15) + a;                         // row
+            const int p = ((a + (combo >> 5)) & 7) + 8 * ((combo >> 4) & 1);  // K group
+            const float4 v = *reinterpret_cast<const float4*>(Araw + i * 64 + 4 * p);
+            float4 h, l;
+            tc::split_tf32(v.x, h.x, l.x);
+            tc::split_tf32(v.y, h.y, l.y);
+            tc::split_tf32(v.z, h.z, l.z);
+            tc::split_tf32(v.w, h.w, l.w);
+            const uint32_t off = (uint32_t)(i >> 3) * UTC_SBO + (uint32_t)p * UTC_LBO + (uint32_t)(i & 7) * 16;
+            *reinterpret_cast<float4*>(Ahi + off) = h;
+            *reinterpret_cast<float4*>(Alo + off) = l;
+          }
+          tc::fence_async_smem();
+        }
+        utc_arrive(&a_full);
+      } else if (is_mma) {
+        bool ok = !*abort_flag;
+        if (ok) ok = utc_wait(&a_full, (uint32_t)g & 1u, abort_flag);
+        if (ok && rt + 1 < nrt) {  // the raw tile has been split: fetch the next one
+          tc::mbar_expect_tx(&raw_full, UTC_OP_BYTES);
+          tc::tma_load_3d(base + 4 * UTC_OP_BYTES, &tmapM, 2 * k0, (rt + 1) * UTC_RT, f, &raw_full);
+          ++tma_issued;
+        }
+        if (ok && g >= 2) ok = utc_wait(&acc_empty[q], (uint32_t)((g - 2) >> 1) & 1u, abort_flag);
+        if (ok) {
+          tc::fence_after_sync();
+          const uint32_t acc = tmem + (uint32_t)q * (2 * UTC_CT);
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint64_t koff = (uint64_t)((kk * 2 * UTC_LBO) >> 4);
+            tc::mma_tf32(acc, dAhi + koff, dBhi + koff, idesc, kk > 0 ? 1u : 0u);
+            tc::mma_tf32(acc, dAhi + koff, dBlo + koff, idesc, 1u);
+            tc::mma_tf32(acc, dAlo + koff, dBhi + koff, idesc, 1u);
+          }
+          tc::mma_commit(&mma_done[q]);
+          issued = g + 1;
+        }
+      } else if (is_epi) {
+        // 1. prefetch: warp w owns tile rows 16w..16w+15; lane l the complex
+        //    columns c0 + 2l, c0 + 2l + 1 (whole 512-byte tile rows per load)
+        const int cl = c0 + 2 * lane;
+        const bool cval = cl < c_end && !(cl >= k0 && cl < k0 + nbk) && !(cl >= ex_lo && cl < ex_hi);
+        float4 cm[16];
+        unsigned rvalid = 0u;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int r = rt * UTC_RT + 16 * warp + u;
+          const bool v = cval && r < b && !(r >= k0 && r < k0 + nbk);
+          rvalid |= (v ? 1u : 0u) << u;
+          cm[u] = v ? *reinterpret_cast<const float4*>(M + (size_t)r * b + cl)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        bool ok = !*abort_flag;
+        if (ok) ok = utc_wait(&mma_done[q], ph, abort_flag);
+        // 2. the previous tile's staging reads are complete
+        utc_epi_sync();
+        if (ok) {
+          // 3. accumulator -> staging: thread = TMEM lane (tile row), 64 of
+          //    the 128 real columns per warp (half h)
+          tc::fence_after_sync();
+          const int wq = warp & 3, h = warp >> 2;
+          const int row = wq * 32 + lane;
+          float* srow = stage + row * UTC_STAGE_LD + h * 64;
+#pragma unroll
+          for (int grp = 0; grp < 4; ++grp) {
+            float v[16];
+            const uint32_t ta = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)q * (2 * UTC_CT) +
+                                (uint32_t)(h * 64 + grp * 16);
+            tc::tmem_ld16(ta, v);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              *reinterpret_cast<float4*>(srow + grp * 16 + 4 * u) =
+                  make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+          }
+          tc::fence_before_sync();
+        }
+        utc_arrive(&acc_empty[q]);
+        // 4. staging complete; 5. add and store the owned rows
+        utc_epi_sync();
+        if (ok) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            if (!(rvalid & (1u << u))) continue;
+            const int row = 16 * warp + u;
+            const float4 a = *reinterpret_cast<const float4*>(stage + row * UTC_STAGE_LD + 4 * lane);
+            float4 m = cm[u];
+            m.x += a.x;
+            m.y += a.y;
+            m.z += a.z;
+            m.w += a.w;
+            *reinterpret_cast<float4*>(M + (size_t)(rt * UTC_RT + row) * b + cl) = m;
+          }
+        }
+      }
+    }
+  }
+  if (is_mma && issued > 0) {
+    // the last commit covers every MMA issued: drain before TMEM is freed
+    const int last = issued - 1;
+    tc::mbar_wait(&mma_done[last & 1], (uint32_t)(last >> 1) & 1u, UTC_WAIT_TRIES);
+  }
+  if (is_mma && tma_issued > 0) {
+    // a raw tile still in flight (after an abort) lands before the CTA exits
+    const int last = tma_issued - 1;
+    tc::mbar_wait(&raw_full, (uint32_t)last & 1u, UTC_WAIT_TRIES);
+  }
+  if (tid == 0 && *abort_flag) atomicExch(err, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
 // G_i[:, perm[c]] = M[:, c];  X_i = G_i C_i with C_i = -L_{i,i+1}.
 template <typename T>
 __global__ void gj_finalize_kernel(OpView op, int i, int RB, const C_t<T>* __restrict__ Mall,
@@ -516,9 +791,32 @@ rr_status factor_impl(rr_factors* fa) {
   // of panel p proceeds on the main stream (disjoint columns of M)
   cudaStream_t st2 = fa->stream2;
   const int P = (b + NB - 1) / NB;
+  // FP32 factors with 32-column panels, b % 8 == 0 (16-byte aligned rows)
+  // and b >= 128 (the TMA map of M) update on the tensor cores;
+  // RR_FP32_SIMT and FP64 on the CUDA cores
+  constexpr bool tc_shape = std::is_same<T, float>::value && NB == 32;
+  const bool use_tc = tc_shape && fa->prec == RR_FP32 && b % 8 == 0 && b >= UTC_RT && fa->tma_m_ok;
+  if (use_tc)
+    RR_CUDA(cudaFuncSetAttribute(gj_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)UTC_SMEM));
   auto update = [&](int k0, int nbk, int cb, int ce, int exl, int exh) {
-    const int ntile = (ce - cb + 63) / 64;
     prof_begin(PROF_UPDATE, st);
+    if constexpr (tc_shape) {
+      if (use_tc) {
+        // one CTA per item (not persistent): CTAs retire after one column
+        // tile, so the look-ahead panel kernel on the second stream finds
+        // free SMs while the update runs
+        const int nct = (ce - cb + UTC_CT - 1) / UTC_CT;
+        const int grid = nct * F;
+        gj_update_tc_kernel<<<grid, UTC_THREADS, UTC_SMEM, st>>>(
+            *reinterpret_cast<const CUtensorMap*>(fa->tmap[2]), b, k0, nbk, cb, ce, exl, exh,
+            reinterpret_cast<float2*>(M),
+            reinterpret_cast<const float2*>(Bbuf), F, nct, fa->flag + F);
+        prof_end(PROF_UPDATE, st);
+        return;
+      }
+    }
+    const int ntile = (ce - cb + 63) / 64;
     gj_update_kernel<T, NB><<<dim3(ntile, (b + 63) / 64, F), 256, 0, st>>>(
         b, k0, nbk, cb, ce, exl, exh, M, Bbuf);
     prof_end(PROF_UPDATE, st);

@@ -5,6 +5,8 @@
 // neighbours (central differences, first-order one-sided at the first/last
 // node, second derivatives re-centred on the inner neighbour there), then the
 // 9 x q x q coefficients of the linearised equations.
+#include <algorithm>
+
 #include "rr_internal.cuh"
 
 namespace {
@@ -170,60 +172,75 @@ __global__ void assemble_kernel(AsmParams p, const double* __restrict__ flow,
 }
 
 // y = (s I - L) x (adjoint: (s I - L)^H x), optionally r = b - that.
-template <bool RESID>
-__global__ void apply_kernel(OpView op, const double2* __restrict__ shifts, int F, int k,
-                             int adjoint, const double2* __restrict__ bvec,
-                             const double2* __restrict__ x, double2* __restrict__ y) {
-  const size_t total = (size_t)F * op.n * k;
+// Block (blockIdx.y = problem f) of rows x columns: a group of tpr threads
+// shares one row n and covers its k columns (coalesced [n][k] accesses, the
+// row's stencil read once per group through L1); all index arithmetic is
+// 32-bit and done once per row; Q (unknowns per point) is a template
+// parameter so the 9 x Q stencil loop unrolls and its loads issue together.
+template <bool RESID, int Q>
+__global__ void __launch_bounds__(256)
+apply_kernel(OpView op, const double2* __restrict__ shifts, int k, int adjoint,
+             const double2* __restrict__ bvec, const double2* __restrict__ x,
+             double2* __restrict__ y) {
+  const int f = blockIdx.y;
+  const int tpr = k < (int)blockDim.x ? k : (int)blockDim.x;
+  const int rows_per = blockDim.x / tpr;
+  const int rsub = threadIdx.x / tpr, jt = threadIdx.x - rsub * tpr;
+  if (rsub >= rows_per) return;
   const size_t NK = (size_t)op.n * k;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    int f = (int)(e / NK);
-    size_t rem = e - (size_t)f * NK;
-    int n = (int)(rem / k);
-    int j = (int)(rem - (size_t)n * k);
-    const double2* xf = x + (size_t)f * NK;
-    double2 s = shifts[f];
-    if (adjoint) s.y = -s.y;
-    double2 acc = cmul(s, xf[(size_t)n * k + j]);
-    int c = n % op.q;
-    int pt = n / op.q;
-    int ix = pt / op.ny, iy = pt % op.ny;
-    if (!adjoint) {
-      const double* cf = op.coef + (size_t)n * op.S;
-      for (int dx = -1; dx <= 1; ++dx) {
-        int jx = ix + dx;
-        if (jx < 0 || jx >= op.nx) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-          int jy = nbr_y(iy, dy, op.ny, op.periodic);
-          if (jy < 0) continue;
-          int base = ((jx * op.ny + jy) * op.q);
-          const double* cs = cf + ((dx + 1) * 3 + (dy + 1)) * op.q;
-          for (int cp = 0; cp < op.q; ++cp)
+  const double2* xf = x + (size_t)f * NK;
+  double2* yf = y + (size_t)f * NK;
+  const double2* bf = RESID ? bvec + (size_t)f * NK : nullptr;
+  double2 s = shifts[f];
+  if (adjoint) s.y = -s.y;
+  constexpr int q = Q, S = 9 * Q;
+  for (int n = blockIdx.x * rows_per + rsub; n < op.n; n += gridDim.x * rows_per) {
+    const int pt = n / q, c = n - pt * q;
+    const int ix = pt / op.ny, iy = pt - ix * op.ny;
+    // neighbour point bases (-1: Dirichlet ghost), slot (dx+1)*3 + (dy+1)
+    int nb[9];
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx)
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int jx = adjoint ? ix - dx : ix + dx;
+        const int jy = nbr_y(iy, adjoint ? -dy : dy, op.ny, op.periodic);
+        nb[(dx + 1) * 3 + (dy + 1)] =
+            (jx >= 0 && jx < op.nx && jy >= 0) ? (jx * op.ny + jy) * q : -1;
+      }
+    const double* cf = op.coef + (size_t)n * S;
+    for (int j = jt; j < k; j += tpr) {
+      double2 acc = cmul(s, xf[(size_t)n * k + j]);
+      if (!adjoint) {
+#pragma unroll
+        for (int sl = 0; sl < 9; ++sl) {
+          const int base = nb[sl];
+          if (base < 0) continue;
+          const double* cs = cf + sl * q;
+#pragma unroll
+          for (int cp = 0; cp < q; ++cp)
             acc = crfma(-cs[cp], xf[(size_t)(base + cp) * k + j], acc);
         }
-      }
-    } else {
-      // (L^T x)[m] = sum over rows r whose stencil reaches m
-      for (int dx = -1; dx <= 1; ++dx) {
-        int rx = ix - dx;
-        if (rx < 0 || rx >= op.nx) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-          int ry = nbr_y(iy, -dy, op.ny, op.periodic);
-          if (ry < 0) continue;
-          int base = (rx * op.ny + ry) * op.q;
-          for (int cr = 0; cr < op.q; ++cr) {
-            double a = op.coef[(size_t)(base + cr) * op.S + ((dx + 1) * 3 + (dy + 1)) * op.q + c];
+      } else {
+        // (L^T x)[n] = sum over rows r whose stencil reaches n: row r at
+        // point (ix - dx, iy - dy) reaches n through its slot (dx, dy)
+#pragma unroll
+        for (int sl = 0; sl < 9; ++sl) {
+          const int base = nb[sl];
+          if (base < 0) continue;
+#pragma unroll
+          for (int cr = 0; cr < q; ++cr) {
+            const double a = op.coef[(size_t)(base + cr) * S + sl * q + c];
             acc = crfma(-a, xf[(size_t)(base + cr) * k + j], acc);
           }
         }
       }
+      if (RESID) {
+        const double2 bb = bf[(size_t)n * k + j];
+        acc = mk(bb.x - acc.x, bb.y - acc.y);
+      }
+      yf[(size_t)n * k + j] = acc;
     }
-    if (RESID) {
-      double2 bb = bvec[e];
-      acc = mk(bb.x - acc.x, bb.y - acc.y);
-    }
-    y[e] = acc;
   }
 }
 
@@ -254,20 +271,25 @@ rr_status launch_assemble(OpDev& d, const rr_grid& g, cudaStream_t st) {
   return RR_OK;
 }
 
-static int grid_for(size_t total, int threads, int dev) {
-  size_t blocks = (total + threads - 1) / threads;
-  size_t cap = (size_t)num_sms(dev) * 16;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  return (int)blocks;
+// Grid of the apply kernel: F problems in y, row blocks in x, about eight
+// 256-thread blocks per SM in total.
+static dim3 apply_grid(const OpDev& d, int F, int k) {
+  const int tpr = k < 256 ? k : 256;
+  const int rows_per = 256 / tpr;
+  long long need = ((long long)d.n + rows_per - 1) / rows_per;
+  long long want = std::max(1LL, (long long)num_sms(d.device) * 8 / std::max(F, 1));
+  return dim3((unsigned)std::max(1LL, std::min(need, want)), (unsigned)F);
 }
 
 rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
                        const double2* x, double2* y, cudaStream_t st) {
-  size_t total = (size_t)F * d.n * k;
   prof_count(1);
-  apply_kernel<false><<<grid_for(total, 256, d.device), 256, 0, st>>>(
-      view(d), shifts, F, k, adjoint, nullptr, x, y);
+  if (d.q == 3)
+    apply_kernel<false, 3><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, adjoint,
+                                                                nullptr, x, y);
+  else
+    apply_kernel<false, 1><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, adjoint,
+                                                                nullptr, x, y);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }
@@ -341,10 +363,13 @@ extern "C" rr_status rr_apply_static(rr_operator* op, int nshift, const double* 
 
 rr_status launch_residual(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
                           const double2* b, const double2* x, double2* r, cudaStream_t st) {
-  size_t total = (size_t)F * d.n * k;
   prof_begin(PROF_RESIDUAL, st);
-  apply_kernel<true><<<grid_for(total, 256, d.device), 256, 0, st>>>(
-      view(d), shifts, F, k, adjoint, b, x, r);
+  if (d.q == 3)
+    apply_kernel<true, 3><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, adjoint, b, x,
+                                                               r);
+  else
+    apply_kernel<true, 1><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, adjoint, b, x,
+                                                               r);
   prof_end(PROF_RESIDUAL, st);
   RR_CUDA(cudaGetLastError());
   return RR_OK;

@@ -92,7 +92,7 @@ rr_status dalloc(P** p, size_t bytes) {
 struct Work {
   double2 *W1, *W2, *W3, *R64;  // [F][N][k] FP64
   void *L1, *L2, *L3;           // [F][N][k] factor precision
-  double2 *G, *R1, *R1i, *R2, *R2i, *Rt, *Ul, *Vr;  // [F][k][k]
+  double2 *G, *R1, *R1i, *R2, *R2i, *Rt, *Ul, *Vr, *Rd;  // [F][k][k]
   double2* part;                // gram partials
   double* dpart;                // norm / max partials
   double *sig, *cond, *bn, *rn; // [F][k] or [F]
@@ -135,6 +135,7 @@ size_t carve(rr_factors* fa, int k, char* base, Work* w) {
   t.Rt = (double2*)take(small);
   t.Ul = (double2*)take(small);
   t.Vr = (double2*)take(small);
+  t.Rd = (double2*)take(small);
   t.part = (double2*)take((size_t)F * nblk_gram * k * k * sizeof(double2));
   t.dpart = (double*)take((size_t)F * nblk_col * k * (sizeof(double) + sizeof(int)));
   t.sig = (double*)take((size_t)F * k * sizeof(double));
@@ -262,7 +263,11 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
 }
 
 // CholeskyQR2 (shifted CholeskyQR3 on breakdown) of Y in place; R = R2 R1 (R3).
-rr_status cholqr2(rr_factors* fa, int k, double2* Y, double2* Rout, Work& w, rr_info* info) {
+// With defer_rinv, the last pass's multiply is left to the caller: Y holds
+// Q R_last (the previous pass's Q) and defer_rinv receives R_last^{-1}, so a
+// caller that needs Q S forms it as Y (R_last^{-1} S) in one multiply.
+rr_status cholqr2(rr_factors* fa, int k, double2* Y, double2* Rout, Work& w, rr_info* info,
+                  double2* defer_rinv = nullptr) {
   const int F = fa->F, N = fa->op->d.n;
   cudaStream_t st = fa->stream;
   rr_status s;
@@ -297,7 +302,11 @@ rr_status cholqr2(rr_factors* fa, int k, double2* Y, double2* Rout, Work& w, rr_
     RR_CUDA(cudaMemsetAsync(w.bad, 0, F * sizeof(int), st));
     if ((s = launch_gram(F, N, k, Y, w.part, w.nblk_gram, w.G, st)) != RR_OK) return s;
     if ((s = launch_cholesky(F, k, w.G, w.R2, w.R2i, w.bad, 0.0, nullptr, st)) != RR_OK) return s;
-    if ((s = launch_right_mul(F, N, k, Y, w.R2i, Y, st)) != RR_OK) return s;
+    if (defer_rinv && p + 1 == passes)
+      RR_CUDA(cudaMemcpyAsync(defer_rinv, w.R2i, (size_t)F * k * k * sizeof(double2),
+                              cudaMemcpyDeviceToDevice, st));
+    else if ((s = launch_right_mul(F, N, k, Y, w.R2i, Y, st)) != RR_OK)
+      return s;
     if ((s = launch_small_mul(F, k, w.R2, w.Rt, w.R1, st)) != RR_OK) return s;
     RR_CUDA(cudaMemcpyAsync(w.Rt, w.R1, (size_t)F * k * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   }
@@ -346,6 +355,31 @@ static int encode_factor_maps(rr_factors* fa) {
                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? 1 : 0;
+}
+
+// TMA map over the FP32 work matrices M [F][b][b] (complex, viewed as floats
+// [F][b][2b]): tiles of 128 rows x 32 complex, the A operand of the
+// tensor-core trailing update.  Needs b >= 128 and b % 8 == 0.
+static int encode_m_map(rr_factors* fa) {
+  const OpDev& d = fa->op->d;
+  if (fa->prec != RR_FP32 || d.b < 128 || (d.b & 7)) return 0;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr) {
+    cudaGetLastError();
+    return 0;
+  }
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * d.b, (cuuint64_t)d.b, (cuuint64_t)fa->F};
+  const cuuint64_t strides[2] = {(cuuint64_t)2 * d.b * 4, (cuuint64_t)2 * d.b * d.b * 4};
+  const cuuint32_t box[3] = {64, 128, 1}, es[3] = {1, 1, 1};
+  CUresult r = encode(reinterpret_cast<CUtensorMap*>(fa->tmap[2]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                      3, fa->M, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 1 : 0;
 }
 
 // ----------------------------------------------------------------- operator
@@ -508,6 +542,7 @@ extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts
     if ((s = dalloc(&fa->Pbuf, (size_t)4 * nshift * 64 * d.b * sizeof(float2))) != RR_OK)
       return fail(s);
     fa->tma_ok = encode_factor_maps(fa);
+    fa->tma_m_ok = encode_m_map(fa);
   }
   if ((s = dalloc(&fa->perm, (size_t)nshift * d.b * sizeof(int))) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->ipiv, (size_t)nshift * 32 * sizeof(int))) != RR_OK) return fail(s);
@@ -694,10 +729,12 @@ extern "C" rr_status rr_sketch_ex(rr_factors* fa, int k, const uint64_t* seeds, 
   if ((s = note(solve_refined(fa, k, 1, w.W1, w.W3, refine_tol, max_refine, w, info))) != RR_OK)
     return s;
   if ((s = launch_scale_rows(F, N, k, d.wisqrt, w.W3, st)) != RR_OK) return s;
-  // svd(B): B^H = Q_B R_B, R_B = Ul S Vr^H  =>  V = Q_B Ul, sigma = S  (fifth step)
-  if ((s = cholqr2(fa, k, w.W3, w.R2i, w, info)) != RR_OK) return s;
+  // svd(B): B^H = Q_B R_B, R_B = Ul S Vr^H  =>  V = Q_B Ul, sigma = S  (fifth step);
+  // Q_B = Y1 R_last^{-1} is not formed: V = Y1 (R_last^{-1} Ul)
+  if ((s = cholqr2(fa, k, w.W3, w.R2i, w, info, w.Rd)) != RR_OK) return s;
   if ((s = launch_jacobi_svd(F, k, w.R2i, w.sig, w.Ul, w.Vr, w.sweeps, st)) != RR_OK) return s;
-  if ((s = launch_right_mul(F, N, k, w.W3, w.Ul, (double2*)V, st)) != RR_OK) return s;
+  if ((s = launch_small_mul(F, k, w.Rd, w.Ul, w.R1, st)) != RR_OK) return s;
+  if ((s = launch_right_mul(F, N, k, w.W3, w.R1, (double2*)V, st)) != RR_OK) return s;
   RR_CUDA(cudaMemcpyAsync(sigma_halko, w.sig, (size_t)F * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
   RR_CUDA(cudaStreamSynchronize(st));
   return conv;
@@ -737,9 +774,10 @@ extern "C" rr_status rr_modes(rr_factors* fa, int k, void* V, void* U, double* s
     if ((s = launch_col_scale(F, N, k, w.W2, sigma, (double2*)U, st)) != RR_OK) return s;
   } else {
     // optional: svd(U Sigma) = U S Vt^H via CholeskyQR2 + Jacobi; V <- V Vt
-    if ((s = cholqr2(fa, k, w.W2, w.R2i, w, info)) != RR_OK) return s;
+    if ((s = cholqr2(fa, k, w.W2, w.R2i, w, info, w.Rd)) != RR_OK) return s;
     if ((s = launch_jacobi_svd(F, k, w.R2i, sigma, w.Ul, w.Vr, w.sweeps, st)) != RR_OK) return s;
-    if ((s = launch_right_mul(F, N, k, w.W2, w.Ul, (double2*)U, st)) != RR_OK) return s;
+    if ((s = launch_small_mul(F, k, w.Rd, w.Ul, w.R1, st)) != RR_OK) return s;
+    if ((s = launch_right_mul(F, N, k, w.W2, w.R1, (double2*)U, st)) != RR_OK) return s;
     if ((s = launch_right_mul(F, N, k, (const double2*)V, w.Vr, (double2*)V, st)) != RR_OK) return s;
   }
   if ((s = launch_finish_modes(F, N, k, (double2*)U, (double2*)V, sigma, w.W1, w.W3, w.dpart,

@@ -120,8 +120,9 @@ struct rr_factors {
   void* Bbuf;        // [F][32][b] saved pivot rows of the current panel
   void* Tbuf;        // [2][F][b][64] staging blocks of one sweep step
   void* Pbuf;        // [4][F][b][64] partial products of the split tensor-core sweep
-  alignas(64) unsigned char tmap[2][128];  // TMA maps of G and of G^H tiles (FP32)
-  int tma_ok;        // 1 if the tensor maps were encoded
+  alignas(64) unsigned char tmap[3][128];  // TMA maps: G tiles, G^H tiles, M row tiles (FP32)
+  int tma_ok;        // 1 if the maps of G were encoded
+  int tma_m_ok;      // 1 if the map of M was encoded
   int* perm;         // [F][b]
   int* ipiv;         // [F][32]
   int* flag;         // [F] singular-pivot flags

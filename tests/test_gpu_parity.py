@@ -88,6 +88,9 @@ SOLVE_CASES = [
     ("ns-24x20", lambda: W.config_small_ns(24, 20).grid, None),
     ("ns-random-11x14", lambda: W.ns_grid(11, 14), "random"),
     ("ns-9x40-four-panels", lambda: W.ns_grid(9, 40), "random"),
+    # b = 264: tensor-core update with ragged row and column tiles and a last
+    # panel of 8 columns
+    ("ns-5x88-ragged-tc-update", lambda: W.ns_grid(5, 88), "random"),
     ("advdiff-periodic", lambda: W.Grid(kind=W.KIND_ADVDIFF, nx=9, ny=12, x0=0, x1=2,
                                         y0=0, y1=3, re=5.0, periodic_y=True), "vconst"),
 ]
@@ -239,12 +242,13 @@ def test_refinement_reports_non_convergence(env):
     assert st == 4
 
 
-@pytest.mark.parametrize("grid_shape", [(24, 20), (9, 40), (8, 50)])
+@pytest.mark.parametrize("grid_shape", [(24, 20), (9, 40), (8, 50), (5, 88), (4, 128)])
 @pytest.mark.parametrize("k", [3, 16, 32])
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_tensor_core_sweeps_match_cuda_core_sweeps(env, grid_shape, k, adjoint):
-    """One unrefined FP32 solve: tcgen05 (3xTF32) sweeps against FP32 CUDA-core
-    sweeps on the same factors' precision, and both against the FP64 oracle."""
+    """One unrefined FP32 solve: the tensor-core path (tcgen05 3xTF32 trailing
+    update when b % 8 == 0, tcgen05 sweeps) against the FP32 CUDA-core path,
+    and both against the FP64 oracle."""
     torch, rr = env
     g = W.ns_grid(*grid_shape)
     flow = W.smooth_random_flow(g, 2)
