@@ -35,8 +35,11 @@ import workloads as W  # noqa: E402
 
 HBM_PEAK_GBS = 6800.0       # profiling-recipe fallback (no MEASURED_PEAKS.json)
 BF16_PEAK_TFLOPS = 1900.0   # fallback burst figure
-SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
-FP32_ALU_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12  # 80.5
+# DRAM bytes (read + write) per launch of the timed kernel class, averaged over
+# its launches, from the ncu captures summarised in profiles/; None until the
+# current kernels have been captured
+UPDATE_TRAFFIC = None
+SWEEP_TRAFFIC = None
 
 
 def parse():
@@ -54,9 +57,10 @@ def parse():
     p.add_argument("--ny", type=int, default=256)
     p.add_argument("--k", type=int, default=32)
     p.add_argument("--roofline-class", default="update")
-    # DRAM bytes per launch of the timed kernel from an ncu capture (see profiles/)
-    p.add_argument("--update-traffic", type=float, default=None)
-    p.add_argument("--sweep-traffic", type=float, default=None)
+    p.add_argument("--workload", default="mixed", choices=["mixed", "batched"],
+                   help="mixed: 512x256, k=32, 64 frequencies (default); "
+                        "batched: the 128-problem uneven batch as one graph")
+    p.add_argument("--tune", type=int, default=1, help="batched: autotune the plan")
     p.add_argument("--breakdown", action="store_true",
                    help="one extra profiled step with every kernel class timed")
     return p.parse_args()
@@ -170,6 +174,18 @@ def update_flops_per_step(b, nx, NB, F):
     for k0 in range(0, b, NB):
         nbk = min(NB, b - k0)
         tot += 8 * (b - nbk) ** 2 * nbk
+    return tot * nx * F
+
+
+def update_bytes_per_step(b, nx, NB, F, csz=8):
+    """Algorithmic HBM bytes of all trailing updates of one factorisation:
+    per panel, one read and one write of every updated M[I,R] entry, one read
+    of the multipliers M[:,K] and of the saved pivot rows B = M[K,R]."""
+    tot = 0
+    for k0 in range(0, b, NB):
+        nbk = min(NB, b - k0)
+        w = b - nbk
+        tot += (w * w * 2 + b * nbk + nbk * w) * csz
     return tot * nx * F
 
 
@@ -313,22 +329,25 @@ def run_ours(args):
         # class; per-launch figures are those totals over the launch count
         tot_s = cls_ms / 1e3
         if args.roofline_class == "update":
+            # rank-32 complex update: 8*32 flops per 16 bytes of M moved
+            # (16 flop/B), far below the TF32 ridge, so HBM bounds it
             NB = panel_width(8, b)
-            work = update_flops_per_step(b, nx, NB, F) * args.steps
-            ach = work / tot_s / 1e12
-            roof = {"kernel": f"gj_update_kernel<float,{NB}> (trailing rank-{NB} complex update)",
-                    "bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP32_ALU_PEAK_TFLOPS,
-                    "traffic": args.update_traffic,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+            work = update_bytes_per_step(b, nx, NB, F) * args.steps
+            flops = update_flops_per_step(b, nx, NB, F) * args.steps
+            ach = work / tot_s / 1e9
+            roof = {"kernel": "gj_update_tc_kernel (trailing rank-32 complex update, "
+                              "tcgen05 kind::tf32, 3xTF32)",
+                    "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "traffic": UPDATE_TRAFFIC, "peak_source": src,
                     "algorithmic_per_launch": work / cls_n, "launches": cls_n,
-                    "avg_launch_us": tot_s / cls_n * 1e6}
+                    "avg_launch_us": tot_s / cls_n * 1e6,
+                    "algorithmic_tflops": flops / tot_s / 1e12}
         elif args.roofline_class == "sweep":
             work = F * (b * b * 8 + 3 * b * k * 8) * cls_n
             ach = work / tot_s / 1e9
             roof = {"kernel": "sweep_tc2_kernel + combine (one streamwise column, tcgen05)",
                     "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": args.sweep_traffic, "peak_source": src,
+                    "frac": ach / hbm, "traffic": SWEEP_TRAFFIC, "peak_source": src,
                     "algorithmic_per_launch": work / cls_n, "launches": cls_n,
                     "avg_launch_us": tot_s / cls_n * 1e6}
 
@@ -434,10 +453,83 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def run_batched(args):
+    """The uneven batching workload: 128 NS problems (grids 128..384 x
+    64..256, k in {8, 16, 32, 64}, omega ~ U[0.1, 8]) as one batch plan (one
+    captured CUDA graph per run), FP32 factors with FP64 refinement; ranks
+    take every world-th problem.  Prints one JSON line."""
+    import torch
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_1902_01458_gb300 import build as rrbuild
+    if rank == 0:
+        rrbuild.build()
+    barrier(pg, local)
+    rrbuild.build()
+    import paper_1902_01458_gb300 as rr
+    from paper_1902_01458_gb300 import _lib
+    rr.load()
+    spec = W.config_batched()
+    mine = [p for i, p in enumerate(spec) if i % world == rank]
+    ops, problems = {}, []
+    for p in mine:
+        if (p.nx, p.ny) not in ops:
+            g = W.ns_grid(p.nx, p.ny)
+            ops[(p.nx, p.ny)] = rr.Operator(g, W.shear_bubble_flow(g), device=local)
+        problems.append({"op": ops[(p.nx, p.ny)], "shift": 1j * p.omega, "k": p.k,
+                         "seed": p.seed})
+    t0 = time.perf_counter()
+    plan = rr.Batch(problems, precision="fp32", tune=bool(args.tune))
+    plan_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        plan.run(stream)
+    torch.cuda.synchronize(dev)
+    barrier(pg, local)
+    _lib.rr_profile_start([])
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    info = None
+    with Clocks(local) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            _, info = plan.run(stream)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    launches = _lib.rr_launch_count()
+    elapsed_s = max_over_ranks(pg, start.elapsed_time(end) / 1e3, dev)
+    value = len(spec) * args.steps / elapsed_s
+    d = plan.describe()
+    if rank == 0:
+        line = {
+            "metric": "resolvent problems/sec, 128-problem uneven batch (mixed FP32+FP64 "
+                      "refinement, one CUDA graph per batch)",
+            "value": value, "unit": "problems/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+f64", "data": "synthetic",
+            "config": {"workload": "ns2d-batch128-uneven", "problems": len(spec),
+                       "grids": "nx in {128,256,384}, ny in {64,128,192,256}, q=3",
+                       "k": "{8,16,32,64}", "omega": "U[0.1, 8]", "generator_seed": 1234,
+                       "l2": "inputs larger than L2 (74 GB of factors)",
+                       "parallelism": f"problem shards x{world}"},
+            "plan": dict(d, plan_s=plan_s, tuned=bool(args.tune)),
+            "clocks": clk.summary(), "gpu_launches": launches,
+            "refine": info,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -278,6 +278,96 @@ rr_status rr_gain_grad(rr_factors* f, int k, int J, const void* U, const void* V
  * a frequency sweep without reallocation.  Errors as rr_factor. */
 rr_status rr_refactor(rr_factors* f, const double* shifts);
 
+/* ------------------------------------------------------------ batch plans
+ * Many resolvent problems of uneven size (grids, shifts, k) as one CUDA
+ * graph.  The paper sweeps the frequency (Sec. IV) with one factorisation
+ * per frequency (Sec. III.A); the frequencies are independent problems, so a
+ * plan runs them together:
+ *  - problems that share an operator form a group with ONE batched block
+ *    factorisation over the group's shifts (as rr_factor);
+ *  - each group is split by k into sub-batches that run Algorithm 1 (as
+ *    rr_sketch then rr_modes with orthogonalize = 0) on the shared factors;
+ *  - rr_batch_create runs every problem once eagerly (calibration), records
+ *    the data-dependent host decisions of that run (the number of FP64
+ *    refinement corrections of every solve, the shifted-CholeskyQR choice of
+ *    every QR), then records the same launch sequence under stream capture,
+ *    with the groups spread over concurrent stream lanes (longest first),
+ *    and instantiates it: rr_batch_run is one cudaGraphLaunch;
+ *  - with opts->tune = 1 the plan is tuned on the device by timing the
+ *    candidates: the trailing-update kernel of each group's factorisation
+ *    (128 x 64 tensor-core tiles or 64 x 64 CUDA-core tiles, on its first
+ *    columns), the K-split (1..4 or the built-in choice) of each
+ *    sub-batch's tensor-core sweep, and the number of lanes (1, 2, 4, 8,
+ *    all groups; whole-graph runs).
+ * A run reproduces the calibration run's arithmetic (same kernels, same
+ * order); after it, the factor flags and a device log of every solve's
+ * final residual and every QR's breakdown flag are checked on the host.
+ *
+ * Problem i: op (problems may share operators; all on one device), shift
+ * s = s_re + i s_im, k in [1, min(64, N)], Philox key seed (the test
+ * matrix of rr_sketch, scaled by the operator's Phi of Eq. 9 when
+ * opts->use_phi), outputs V, U (device complex128 [N][k]), sigma and
+ * sigma_halko (device [k]; sigma_halko may be NULL) as rr_sketch /
+ * rr_modes define them.  The plan keeps the problems' pointers: outputs are
+ * written on every run, and the operators must outlive the plan. */
+typedef struct rr_batch rr_batch;
+
+typedef struct {
+  rr_operator* op;
+  double s_re, s_im;
+  int k;
+  uint64_t seed;
+  void* V;
+  void* U;
+  double* sigma;
+  double* sigma_halko;
+} rr_problem;
+
+typedef struct {
+  int use_phi;        /* 1: test matrix scaled by Phi (Eq. 9)              */
+  double refine_tol;  /* FP64 refinement tolerance (FP32 factors)          */
+  int max_refine;     /* refinement cap per solve                          */
+  int tune;           /* 1: time candidate schedules on the device         */
+  int lanes;          /* concurrent lanes; 0: tuned, or min(groups, 4)     */
+} rr_batch_opts;
+
+typedef struct {
+  int groups;             /* operators (one factorisation each)             */
+  int views;              /* (operator, k) sub-batches                      */
+  int lanes;              /* stream lanes of the captured graph             */
+  int graph_nodes;        /* nodes of the graph                             */
+  int kernel_nodes;       /* kernel launches per rr_batch_run               */
+  int cuda_core_updates;  /* groups tuned to the CUDA-core trailing update  */
+  double plan_ms;         /* host wall time of rr_batch_create              */
+  double tuned_ms;        /* best whole-graph time seen by the lane tuner   */
+} rr_batch_desc;
+
+/* Build a plan (calibration run, optional tuning, capture, one validation
+ * run).  opts NULL = {use_phi 1, refine_tol 1e-10, max_refine 10, tune 0,
+ * lanes 0}.  Errors: RR_ERR_ARG (no problems, null pointers, k out of
+ * range, operators on different devices, non-finite shifts, lanes outside
+ * [0, 64]), RR_ERR_NOMEM, RR_ERR_SINGULAR, RR_ERR_RANK, RR_ERR_TIMEOUT,
+ * RR_ERR_CUDA; *out is NULL on error. */
+rr_status rr_batch_create(int nprob, const rr_problem* probs, rr_precision prec,
+                          const rr_batch_opts* opts, rr_batch** out);
+
+/* Run the plan's graph on stream (NULL: the plan's own stream), wait for it
+ * and check it: RR_ERR_SINGULAR / RR_ERR_TIMEOUT from the factor flags,
+ * RR_ERR_RANK from a QR breakdown, RR_ERR_NOCONV when some solve's final
+ * relative residual exceeds both refine_tol and 4x the one the calibration
+ * run reached (possible only after rr_batch_set_shifts: rebuild the plan).
+ * info (may be NULL): largest residual, corrections and condition estimate. */
+rr_status rr_batch_run(rr_batch* b, void* stream, rr_info* info);
+
+/* Replace the shifts of all problems (host, 2*nprob doubles, problem order)
+ * for later runs: the graph reads them from device memory, so a frequency
+ * sweep reuses one plan.  The refinement schedule stays the calibrated one
+ * (checked by rr_batch_run). */
+rr_status rr_batch_set_shifts(rr_batch* b, const double* shifts);
+
+rr_status rr_batch_describe(const rr_batch* b, rr_batch_desc* desc);
+rr_status rr_batch_destroy(rr_batch* b);
+
 /* Instrumentation (no counterpart in the paper).  rr_launch_count: kernels
  * launched by this library in this process since the last rr_profile_start.
  * rr_profile_start(mask): reset the counters and time every later launch of

@@ -63,6 +63,28 @@ class rr_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class rr_problem(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_void_p), ("s_re", ctypes.c_double), ("s_im", ctypes.c_double),
+                ("k", ctypes.c_int), ("seed", ctypes.c_uint64), ("V", ctypes.c_void_p),
+                ("U", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+                ("sigma_halko", ctypes.c_void_p)]
+
+
+class rr_batch_opts(ctypes.Structure):
+    _fields_ = [("use_phi", ctypes.c_int), ("refine_tol", ctypes.c_double),
+                ("max_refine", ctypes.c_int), ("tune", ctypes.c_int), ("lanes", ctypes.c_int)]
+
+
+class rr_batch_desc(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_int), ("views", ctypes.c_int), ("lanes", ctypes.c_int),
+                ("graph_nodes", ctypes.c_int), ("kernel_nodes", ctypes.c_int),
+                ("cuda_core_updates", ctypes.c_int), ("plan_ms", ctypes.c_double),
+                ("tuned_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # exported symbol -> (restype, argtypes)
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -93,6 +115,12 @@ SIGNATURES = {
     "rr_gaussian": (_I, [_I, _I, _I, ctypes.POINTER(ctypes.c_uint64), _P, _P, _P]),
     "rr_refactor": (_I, [_P, ctypes.POINTER(ctypes.c_double)]),
     "rr_gain_grad": (_I, [_P, _I, _I, _P, _P, _P, _D, _I, _P, ctypes.POINTER(rr_info)]),
+    "rr_batch_create": (_I, [_I, ctypes.POINTER(rr_problem), _I,
+                             ctypes.POINTER(rr_batch_opts), ctypes.POINTER(_P)]),
+    "rr_batch_run": (_I, [_P, _P, ctypes.POINTER(rr_info)]),
+    "rr_batch_set_shifts": (_I, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "rr_batch_describe": (_I, [_P, ctypes.POINTER(rr_batch_desc)]),
+    "rr_batch_destroy": (_I, [_P]),
     "rr_launch_count": (ctypes.c_longlong, []),
     "rr_profile_start": (_I, [ctypes.c_uint]),
     "rr_profile_read": (_I, [_I, ctypes.POINTER(ctypes.c_double),
@@ -426,3 +454,66 @@ class Factors:
         U, sig, i2 = self.modes(V, orthogonalize, refine_tol, max_refine)
         info = {key: max(i1[key], i2[key]) for key in i1}
         return ResolventResult(sig, sh, U, V, info)
+
+
+class Batch:
+    """Owns an rr_batch plan: problems of uneven size (operators, shifts, k)
+    run as one captured CUDA graph.  Outputs are allocated here per problem
+    (V, U [N, k] complex128; sigma, sigma_halko [k] float64, on the device) and
+    rewritten by every run()."""
+
+    def __init__(self, problems, precision="fp32", use_phi=True, refine_tol=1e-10,
+                 max_refine=10, tune=False, lanes=0):
+        import torch
+        self.problems = list(problems)
+        if not self.problems:
+            raise ValueError("a batch needs at least one problem")
+        self.outputs = []
+        arr = (rr_problem * len(self.problems))()
+        for i, p in enumerate(self.problems):
+            op, shift, k, seed = p["op"], complex(p["shift"]), int(p["k"]), int(p["seed"])
+            dev = f"cuda:{op.device}"
+            out = {"V": torch.empty(op.n, k, dtype=torch.complex128, device=dev),
+                   "U": torch.empty(op.n, k, dtype=torch.complex128, device=dev),
+                   "sigma": torch.empty(k, dtype=torch.float64, device=dev),
+                   "sigma_halko": torch.empty(k, dtype=torch.float64, device=dev)}
+            self.outputs.append(out)
+            arr[i] = rr_problem(op.handle.value if hasattr(op.handle, "value") else op.handle,
+                                shift.real, shift.imag, k, seed, _dptr(out["V"]),
+                                _dptr(out["U"]), _dptr(out["sigma"]),
+                                _dptr(out["sigma_halko"]))
+        opts = rr_batch_opts(int(bool(use_phi)), float(refine_tol), int(max_refine),
+                             int(bool(tune)), int(lanes))
+        h = ctypes.c_void_p()
+        _check(load().rr_batch_create(len(self.problems), arr, PRECISION[precision],
+                                      ctypes.byref(opts), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None, check=True):
+        info = rr_info()
+        st = load().rr_batch_run(self.handle, _stream_ptr(stream), ctypes.byref(info))
+        if check:
+            _check(st)
+        return st, info.as_dict()
+
+    def set_shifts(self, shifts):
+        s = np.asarray(shifts, dtype=np.complex128).ravel()
+        if s.size != len(self.problems):
+            raise ValueError("one shift per problem")
+        _check(load().rr_batch_set_shifts(self.handle, _shift_array(s)))
+
+    def describe(self) -> dict:
+        d = rr_batch_desc()
+        _check(load().rr_batch_describe(self.handle, ctypes.byref(d)))
+        return d.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load().rr_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -78,7 +78,7 @@ __device__ __forceinline__ void amax_merge(T& v, int& i, T v2, int i2) {
 // original row ("slot"); the LU with partial pivoting over slots >= k0 never
 // moves data: each step picks the largest remaining |.|^2 of column j (lowest
 // slot on ties), marks that slot as the j-th pivot and eliminates column j
-// from the other remaining slots, with two block barriers per step (every
+// from the other remaining slots, with one block barrier per step (every
 // warp reduces the per-warp candidates itself).  Warp 0 then replays the
 // choices as the equivalent sequence of row interchanges (ipiv, as the row
 // block kernel applies them to the other columns) and the final position of
@@ -97,8 +97,8 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* P = reinterpret_cast<C*>(smem_raw);  // [b][PS] by slot
   __shared__ C Ui[NB][NB + 1], Li[NB][NB + 1], Ti[NB][NB + 1];
-  __shared__ T red_v[NW];
-  __shared__ int red_i[NW];
+  __shared__ T red_v[2][NW];  // per-step candidates, double buffered by step parity
+  __shared__ int red_i[2][NW];
   __shared__ int chosen[NB];
   __shared__ int sigK[NB];            // slot that ends at position k0 + j
   __shared__ int nkPos[32], nkSlot[32];
@@ -133,10 +133,13 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
       int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
       amax_merge(bv, bi, v2, i2);
     }
-    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+    // one barrier per step: it publishes the candidates and orders the
+    // owner's elimination of step j-1 on the pivot row before its reads
+    // below; the other rows are only ever touched by their owner thread
+    if (lane == 0) { red_v[j & 1][warp] = bv; red_i[j & 1][warp] = bi; }
     __syncthreads();
-    bv = lane < NW ? red_v[lane] : (T)-1;
-    bi = lane < NW ? red_i[lane] : b;
+    bv = lane < NW ? red_v[j & 1][lane] : (T)-1;
+    bi = lane < NW ? red_i[j & 1][lane] : b;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       T v2 = __shfl_xor_sync(0xffffffffu, bv, o);
@@ -162,8 +165,8 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
       for (int c = 0; c < NB; ++c)
         if (c > j && c < nbk) P[r * PS + c] = csub(P[r * PS + c], cmul(l, P[p * PS + c]));
     }
-    __syncthreads();
   }
+  __syncthreads();
 
   // warp 0: replay the choices as row interchanges (position a = k0 + j with
   // the current position q of the chosen slot), tracking where slots end
@@ -435,9 +438,9 @@ gj_update_kernel(int b, int k0, int nbk, int c_begin, int c_end, int ex_lo, int 
 // the right operand is B expanded to B~ with rows (Re, -Im), (Im, Re) per
 // complex column, so one real product gives the complex one.  FP32 accuracy
 // comes from the 3xTF32 split (hi.hi + hi.lo + lo.hi into one FP32 TMEM
-// accumulator).  One CTA per item (problem, tile of 64 complex columns): it
-// expands B~ once and streams the row tiles of M through a warp-specialised
-// pipeline:
+// accumulator).  One CTA per item (problem, tile of 64 complex columns,
+// group of row tiles): it expands B~ once and streams the item's row tiles
+// of M through a warp-specialised pipeline:
 //   warp 10     loads the raw A tile of row tile t+1 by TMA (3-D map over M)
 //               and issues the 24 MMAs of tile t into accumulator t & 1,
 //   warps 8-9   split the raw A tile into the hi / lo operand tiles,
@@ -482,7 +485,7 @@ __device__ __forceinline__ void utc_epi_sync() {
 __global__ void __launch_bounds__(UTC_THREADS, 1)
 gj_update_tc_kernel(const __grid_constant__ CUtensorMap tmapM, int b, int k0, int nbk, int c_begin,
                     int c_end, int ex_lo, int ex_hi, float2* __restrict__ Mall,
-                    const float2* __restrict__ Ball, int F, int nct, int* err) {
+                    const float2* __restrict__ Ball, int F, int nct, int nrg, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t raw_full, a_full, mma_done[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
@@ -501,7 +504,8 @@ gj_update_tc_kernel(const __grid_constant__ CUtensorMap tmapM, int b, int k0, in
   const bool is_conv = tid >= UTC_EPI && tid < UTC_EPI + UTC_CONV;
   const bool is_mma = tid == UTC_EPI + UTC_CONV;
   const int nrt = (b + UTC_RT - 1) / UTC_RT;
-  const int nitems = nct * F;
+  const int rpg = (nrt + nrg - 1) / nrg;  // row tiles per row group
+  const int nitems = nct * F * nrg;
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
   if (tid == 0) {
@@ -529,7 +533,9 @@ gj_update_tc_kernel(const __grid_constant__ CUtensorMap tmapM, int b, int k0, in
   int issued = 0;      // tiles whose MMAs were issued (MMA thread)
   int tma_issued = 0;  // raw A tiles requested (MMA thread)
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int f = it / nct, ct = it - f * nct;
+    const int rg = it % nrg, fc = it / nrg;
+    const int f = fc / nct, ct = fc - f * nct;
+    const int rt0 = rg * rpg, rt1 = min(nrt, rt0 + rpg);
     const int c0 = c_begin + ct * UTC_CT;
     float2* M = Mall + (size_t)f * b * b;
     // every earlier tile's MMAs are complete here (their epilogues waited
@@ -561,12 +567,12 @@ gj_update_tc_kernel(const __grid_constant__ CUtensorMap tmapM, int b, int k0, in
       tc::fence_async_smem();
     }
     __syncthreads();
-    if (is_mma && !*abort_flag) {  // raw A tile of the item's first row tile
+    if (is_mma && !*abort_flag && rt0 < rt1) {  // raw A tile of the item's first row tile
       tc::mbar_expect_tx(&raw_full, UTC_OP_BYTES);
-      tc::tma_load_3d(base + 4 * UTC_OP_BYTES, &tmapM, 2 * k0, 0, f, &raw_full);
+      tc::tma_load_3d(base + 4 * UTC_OP_BYTES, &tmapM, 2 * k0, rt0 * UTC_RT, f, &raw_full);
       ++tma_issued;
     }
-    for (int rt = 0; rt < nrt; ++rt, ++g) {
+    for (int rt = rt0; rt < rt1; ++rt, ++g) {
       const int q = g & 1;
       const uint32_t ph = (uint32_t)(g >> 1) & 1u;  // phase of tile g on the barriers q
       if (is_conv) {
@@ -604,7 +610,7 @@ gj_update_tc_kernel(const __grid_constant__ CUtensorMap tmapM, int b, int k0, in
       } else if (is_mma) {
         bool ok = !*abort_flag;
         if (ok) ok = utc_wait(&a_full, (uint32_t)g & 1u, abort_flag);
-        if (ok && rt + 1 < nrt) {  // the raw tile has been split: fetch the next one
+        if (ok && rt + 1 < rt1) {  // the raw tile has been split: fetch the next one
           tc::mbar_expect_tx(&raw_full, UTC_OP_BYTES);
           tc::tma_load_3d(base + 4 * UTC_OP_BYTES, &tmapM, 2 * k0, (rt + 1) * UTC_RT, f, &raw_full);
           ++tma_issued;
@@ -795,7 +801,8 @@ rr_status factor_impl(rr_factors* fa) {
   // and b >= 128 (the TMA map of M) update on the tensor cores;
   // RR_FP32_SIMT and FP64 on the CUDA cores
   constexpr bool tc_shape = std::is_same<T, float>::value && NB == 32;
-  const bool use_tc = tc_shape && fa->prec == RR_FP32 && b % 8 == 0 && b >= UTC_RT && fa->tma_m_ok;
+  const bool use_tc = tc_shape && fa->prec == RR_FP32 && b % 8 == 0 && b >= UTC_RT &&
+                      fa->tma_m_ok && fa->tune_update != 1;
   if (use_tc)
     RR_CUDA(cudaFuncSetAttribute(gj_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)UTC_SMEM));
@@ -806,12 +813,15 @@ rr_status factor_impl(rr_factors* fa) {
         // one CTA per item (not persistent): CTAs retire after one column
         // tile, so the look-ahead panel kernel on the second stream finds
         // free SMs while the update runs
+        // a slice of one column tile (the next panel's columns) splits its
+        // row tiles over CTAs: it is on the look-ahead critical path
         const int nct = (ce - cb + UTC_CT - 1) / UTC_CT;
-        const int grid = nct * F;
+        const int nrg = nct == 1 ? (b + UTC_RT - 1) / UTC_RT : 1;
+        const int grid = nct * F * nrg;
         gj_update_tc_kernel<<<grid, UTC_THREADS, UTC_SMEM, st>>>(
             *reinterpret_cast<const CUtensorMap*>(fa->tmap[2]), b, k0, nbk, cb, ce, exl, exh,
             reinterpret_cast<float2*>(M),
-            reinterpret_cast<const float2*>(Bbuf), F, nct, fa->flag + F);
+            reinterpret_cast<const float2*>(Bbuf), F, nct, nrg, fa->flag + F);
         prof_end(PROF_UPDATE, st);
         return;
       }
@@ -828,7 +838,9 @@ rr_status factor_impl(rr_factors* fa) {
                                                           fa->flag);
     prof_end(PROF_PANEL, s);
   };
-  for (int i = 0; i < nx; ++i) {
+  // (factor_cols > 0 stops after that many columns: autotuner timing only)
+  const int ncols = fa->factor_cols > 0 ? std::min(fa->factor_cols, nx) : nx;
+  for (int i = 0; i < ncols; ++i) {
     iota_kernel<<<(b * F + 255) / 256, 256, 0, st>>>(fa->perm, b, F);
     prof_count(1);
     dim3 gs((b + 127) / 128, b, F);

@@ -11,11 +11,19 @@ std::vector<cudaEvent_t> g_start[PROF_N], g_stop[PROF_N];
 size_t g_used[PROF_N] = {0};
 long long g_class_launches[PROF_N] = {0};
 long long g_launches = 0;
+
+int g_suspended = 0;
 }  // namespace
 
-void prof_count(int n) { g_launches += n; }
+ProfSuspend::ProfSuspend() { ++g_suspended; }
+ProfSuspend::~ProfSuspend() { --g_suspended; }
+
+void prof_count(int n) {
+  if (!g_suspended) g_launches += n;
+}
 
 void prof_begin(int cls, cudaStream_t st) {
+  if (g_suspended) return;
   g_launches += 1;
   g_class_launches[cls] += 1;
   if (!(g_mask & (1u << cls))) return;
@@ -31,7 +39,7 @@ void prof_begin(int cls, cudaStream_t st) {
 }
 
 void prof_end(int cls, cudaStream_t st) {
-  if (!(g_mask & (1u << cls))) return;
+  if (g_suspended || !(g_mask & (1u << cls))) return;
   size_t i = g_used[cls];
   if (i >= g_stop[cls].size()) return;
   cudaEventRecord(g_stop[cls][i], st);

@@ -199,9 +199,42 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
     if ((s = launch_solve_lo(fa, k, adjoint, w.L1, w.L2, w.L3)) != RR_OK) return s;
     if ((s = launch_convert_f2d(nel, (const float2*)w.L2, x, 0, st)) != RR_OK) return s;
   }
-  const bool check = lo || info != nullptr || tol > 0.0;
+  const bool check = lo || info != nullptr || tol > 0.0 || fa->sched_mode != SCHED_EAGER;
   if (!check) return RR_OK;
   if ((s = launch_colnorm2(F, d.n, k, b, w.dpart, w.nblk_col, w.bn, st)) != RR_OK) return s;
+  if (fa->sched_mode == SCHED_REPLAY) {
+    // the recorded number of corrections, no host reads; the final residual
+    // and right-hand-side norms go to the check log
+    if (fa->sched_pos >= fa->sched->size()) {
+      g_err = "graph schedule exhausted (launch sequence differs from the recorded one)";
+      return RR_ERR_ARG;
+    }
+    const int nit = (*fa->sched)[fa->sched_pos++];
+    for (int t = 0; t < nit; ++t) {
+      if ((s = launch_residual(d, F, fa->shifts, k, adjoint, b, x, w.R64, st)) != RR_OK) return s;
+      if (!lo) {
+        if ((s = launch_solve_lo(fa, k, adjoint, w.R64, w.L2, w.L3)) != RR_OK) return s;
+        if ((s = launch_axpy(nel, (const double2*)w.L2, x, st)) != RR_OK) return s;
+      } else {
+        if ((s = launch_convert_d2f(nel, w.R64, (float2*)w.L1, st)) != RR_OK) return s;
+        if ((s = launch_solve_lo(fa, k, adjoint, w.L1, w.L2, w.L3)) != RR_OK) return s;
+        if ((s = launch_convert_f2d(nel, (const float2*)w.L2, x, 1, st)) != RR_OK) return s;
+      }
+    }
+    if ((s = launch_residual(d, F, fa->shifts, k, adjoint, b, x, w.R64, st)) != RR_OK) return s;
+    if ((s = launch_colnorm2(F, d.n, k, w.R64, w.dpart, w.nblk_col, w.rn, st)) != RR_OK) return s;
+    const size_t nb = (size_t)F * k * sizeof(double);
+    if (fa->chk_off + 2 * nb > fa->chk_cap) {
+      g_err = "graph check log too small";
+      return RR_ERR_ARG;
+    }
+    RR_CUDA(cudaMemcpyAsync(fa->chk + fa->chk_off, w.bn, nb, cudaMemcpyDeviceToDevice, st));
+    RR_CUDA(cudaMemcpyAsync(fa->chk + fa->chk_off + nb, w.rn, nb, cudaMemcpyDeviceToDevice, st));
+    fa->chk_desc->insert(fa->chk_desc->end(), {CHK_SOLVE, (long long)fa->chk_off, (long long)F * k});
+    fa->chk_off += 2 * nb;
+    return RR_OK;
+  }
+  if (fa->sched_mode == SCHED_RECORD) fa->chk_need += 2 * (size_t)F * k * sizeof(double);
   std::vector<double> bn((size_t)F * k), rn((size_t)F * k);
   RR_CUDA(cudaMemcpyAsync(bn.data(), w.bn, bn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   int it = 0;
@@ -259,6 +292,7 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
     info->refine_residual = std::max(info->refine_residual, rel);
     info->refine_stagnated |= stagnated;
   }
+  if (fa->sched_mode == SCHED_RECORD) fa->sched->push_back(it);
   return result;
 }
 
@@ -274,13 +308,26 @@ rr_status cholqr2(rr_factors* fa, int k, double2* Y, double2* Rout, Work& w, rr_
   RR_CUDA(cudaMemsetAsync(w.bad, 0, F * sizeof(int), st));
   if ((s = launch_gram(F, N, k, Y, w.part, w.nblk_gram, w.G, st)) != RR_OK) return s;
   if ((s = launch_cholesky(F, k, w.G, w.R1, w.R1i, w.bad, 0.0, w.cond, st)) != RR_OK) return s;
+  const bool replay = fa->sched_mode == SCHED_REPLAY;
   std::vector<int> bad(F);
   std::vector<double> cond(F);
-  RR_CUDA(cudaMemcpyAsync(bad.data(), w.bad, F * sizeof(int), cudaMemcpyDeviceToHost, st));
-  RR_CUDA(cudaMemcpyAsync(cond.data(), w.cond, F * sizeof(double), cudaMemcpyDeviceToHost, st));
-  RR_CUDA(cudaStreamSynchronize(st));
   bool any_bad = false;
-  for (int f = 0; f < F; ++f) any_bad |= bad[f] != 0;
+  if (replay) {
+    if (fa->sched_pos >= fa->sched->size()) {
+      g_err = "graph schedule exhausted (launch sequence differs from the recorded one)";
+      return RR_ERR_ARG;
+    }
+    any_bad = (*fa->sched)[fa->sched_pos++] != 0;
+  } else {
+    RR_CUDA(cudaMemcpyAsync(bad.data(), w.bad, F * sizeof(int), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaMemcpyAsync(cond.data(), w.cond, F * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    for (int f = 0; f < F; ++f) any_bad |= bad[f] != 0;
+    if (fa->sched_mode == SCHED_RECORD) {
+      fa->sched->push_back(any_bad ? 1 : 0);
+      fa->chk_need += (size_t)F * (sizeof(double) + sizeof(double));
+    }
+  }
   int passes = 2;
   if (any_bad) {
     // shifted CholeskyQR (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa,
@@ -310,13 +357,27 @@ rr_status cholqr2(rr_factors* fa, int k, double2* Y, double2* Rout, Work& w, rr_
     if ((s = launch_small_mul(F, k, w.R2, w.Rt, w.R1, st)) != RR_OK) return s;
     RR_CUDA(cudaMemcpyAsync(w.Rt, w.R1, (size_t)F * k * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   }
-  RR_CUDA(cudaMemcpyAsync(bad.data(), w.bad, F * sizeof(int), cudaMemcpyDeviceToHost, st));
-  RR_CUDA(cudaStreamSynchronize(st));
-  for (int f = 0; f < F; ++f)
-    if (bad[f]) {
-      g_err = "CholeskyQR breakdown: the sketch is numerically rank deficient";
-      return RR_ERR_RANK;
+  if (replay) {
+    // breakdown flags and the first pass's condition estimate, checked after
+    // the graph has run
+    const size_t nb = (size_t)F * sizeof(double);
+    if (fa->chk_off + 2 * nb > fa->chk_cap) {
+      g_err = "graph check log too small";
+      return RR_ERR_ARG;
     }
+    RR_CUDA(cudaMemcpyAsync(fa->chk + fa->chk_off, w.bad, F * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    RR_CUDA(cudaMemcpyAsync(fa->chk + fa->chk_off + nb, w.cond, nb, cudaMemcpyDeviceToDevice, st));
+    fa->chk_desc->insert(fa->chk_desc->end(), {CHK_CQR, (long long)fa->chk_off, (long long)F});
+    fa->chk_off += 2 * nb;
+  } else {
+    RR_CUDA(cudaMemcpyAsync(bad.data(), w.bad, F * sizeof(int), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    for (int f = 0; f < F; ++f)
+      if (bad[f]) {
+        g_err = "CholeskyQR breakdown: the sketch is numerically rank deficient";
+        return RR_ERR_RANK;
+      }
+  }
   if (Rout)
     RR_CUDA(cudaMemcpyAsync(Rout, w.Rt, (size_t)F * k * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   return RR_OK;
@@ -593,7 +654,13 @@ extern "C" rr_status rr_destroy_factors(rr_factors* fa) {
   if (!fa) return RR_OK;
   DeviceGuard guard(fa->op->d.device);
   if (fa->stream) cudaStreamSynchronize(fa->stream);
-  cudaFree(fa->G);
+  if (!fa->is_view) {
+    cudaFree(fa->G);
+    cudaFree(fa->shifts);
+  }
+  cudaFree(fa->chk);
+  delete fa->sched;
+  delete fa->chk_desc;
   cudaFree(fa->X);
   cudaFree(fa->M);
   cudaFree(fa->Bbuf);
@@ -602,7 +669,6 @@ extern "C" rr_status rr_destroy_factors(rr_factors* fa) {
   cudaFree(fa->perm);
   cudaFree(fa->ipiv);
   cudaFree(fa->flag);
-  cudaFree(fa->shifts);
   cudaFree(fa->ws);
   if (fa->stream2) {
     cudaStreamSynchronize(fa->stream2);
@@ -612,6 +678,107 @@ extern "C" rr_status rr_destroy_factors(rr_factors* fa) {
   if (fa->ev_panel) cudaEventDestroy(fa->ev_panel);
   delete[] fa->shifts_h;
   delete fa;
+  return RR_OK;
+}
+
+// ------------------------------------------------ batch-plan internals
+// View over shifts [f0, f0 + nf) of parent factors: shares G and the device
+// shifts, owns staging buffers, flags, workspace and TMA maps.
+rr_status factors_view(rr_factors* parent, int f0, int nf, cudaStream_t st, rr_factors** out) {
+  *out = nullptr;
+  if (!parent || parent->is_view || f0 < 0 || nf < 1 || f0 + nf > parent->F)
+    return arg_error("factors_view: bad range");
+  DeviceGuard guard(parent->op->d.device);
+  const OpDev& d = parent->op->d;
+  rr_factors* v = new rr_factors();
+  std::memset(v, 0, sizeof(*v));
+  v->op = parent->op;
+  v->F = nf;
+  v->prec = parent->prec;
+  v->stream = st;
+  v->csz = parent->csz;
+  v->is_view = 1;
+  v->G = static_cast<char*>(parent->G) + (size_t)f0 * d.nx * d.b * d.b * parent->csz;
+  v->shifts = parent->shifts + f0;
+  v->tune_update = parent->tune_update;
+  rr_status s;
+  auto fail = [&](rr_status r) {
+    rr_destroy_factors(v);
+    return r;
+  };
+  if ((s = dalloc(&v->Tbuf, (size_t)nf * 128 * d.b * v->csz)) != RR_OK) return fail(s);
+  if (v->prec == RR_FP32) {
+    if ((s = dalloc(&v->Pbuf, (size_t)4 * nf * 64 * d.b * sizeof(float2))) != RR_OK) return fail(s);
+    v->tma_ok = encode_factor_maps(v);
+  }
+  if ((s = dalloc(&v->flag, (size_t)(nf + 1) * sizeof(int))) != RR_OK) return fail(s);
+  RR_CUDA(cudaMemsetAsync(v->flag, 0, (nf + 1) * sizeof(int), st));
+  v->shifts_h = new double2[nf];
+  for (int f = 0; f < nf; ++f) v->shifts_h[f] = parent->shifts_h[f0 + f];
+  v->sched = new std::vector<int>();
+  v->chk_desc = new std::vector<long long>();
+  *out = v;
+  return RR_OK;
+}
+
+// Factorisation launches only (flags cleared first, no host synchronisation):
+// the form a graph captures.  Flags are read by factor_flags afterwards.
+rr_status factor_async(rr_factors* fa) {
+  if (fa->is_view) return arg_error("factor_async: a view cannot be factored");
+  DeviceGuard guard(fa->op->d.device);
+  RR_CUDA(cudaMemsetAsync(fa->flag, 0, (fa->F + 1) * sizeof(int), fa->stream));
+  return launch_factor(fa);
+}
+
+rr_status factor_flags(rr_factors* fa) {
+  DeviceGuard guard(fa->op->d.device);
+  std::vector<int> flags(fa->F + 1);
+  RR_CUDA(cudaMemcpy(flags.data(), fa->flag, (fa->F + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  if (flags[fa->F]) {
+    g_err = "a tensor-core update kernel timed out waiting for its MMAs";
+    return RR_ERR_TIMEOUT;
+  }
+  for (int f = 0; f < fa->F; ++f)
+    if (flags[f]) {
+      g_err = "exact zero pivot in a batched factorisation";
+      return RR_ERR_SINGULAR;
+    }
+  return RR_OK;
+}
+
+// Workspace for k columns allocated ahead of a capture (no allocation may
+// happen while a graph is recorded).
+rr_status factors_reserve(rr_factors* fa, int k) {
+  DeviceGuard guard(fa->op->d.device);
+  Work w;
+  return get_work(fa, k, &w);
+}
+
+// Milliseconds of one unrefined forward solve with k columns on zeroed
+// inputs (autotuner timing of the sweep schedule); the first run warms up.
+rr_status time_solve(rr_factors* fa, int k, float* ms) {
+  DeviceGuard guard(fa->op->d.device);
+  Work w;
+  rr_status s = get_work(fa, k, &w);
+  if (s != RR_OK) return s;
+  cudaStream_t st = fa->stream;
+  const size_t nel = (size_t)fa->F * fa->op->d.n * k;
+  RR_CUDA(cudaMemsetAsync(w.L1, 0, nel * fa->csz, st));
+  cudaEvent_t e0, e1;
+  RR_CUDA(cudaEventCreate(&e0));
+  RR_CUDA(cudaEventCreate(&e1));
+  s = launch_solve_lo(fa, k, 0, w.L1, w.L2, w.L3);
+  if (s == RR_OK) {
+    cudaEventRecord(e0, st);
+    s = launch_solve_lo(fa, k, 0, w.L1, w.L2, w.L3);
+    cudaEventRecord(e1, st);
+  }
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (s == RR_OK && e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != RR_OK) return s;
+  if (e != cudaSuccess) return cuda_status(e, "time_solve");
   return RR_OK;
 }
 
@@ -690,7 +857,9 @@ extern "C" rr_status rr_sketch_ex(rr_factors* fa, int k, const uint64_t* seeds, 
     if (r == RR_ERR_NOCONV) conv = r;
     return r == RR_ERR_NOCONV ? RR_OK : r;
   };
-  RR_CUDA(cudaMemcpyAsync(w.seeds, seeds, F * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  // (replayed launch sequences reuse the seeds the recording run uploaded)
+  if (fa->sched_mode != SCHED_REPLAY)
+    RR_CUDA(cudaMemcpyAsync(w.seeds, seeds, F * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
   // Omega' = W^{-1/2} diag(phi) Omega  (first step, Eq. 9)
   if (kind == RR_OMEGA_ORTHONORMAL) {
     // Omega = Q factor of diag(phi) randn (CholeskyQR2), then weighted
@@ -736,7 +905,7 @@ extern "C" rr_status rr_sketch_ex(rr_factors* fa, int k, const uint64_t* seeds, 
   if ((s = launch_small_mul(F, k, w.Rd, w.Ul, w.R1, st)) != RR_OK) return s;
   if ((s = launch_right_mul(F, N, k, w.W3, w.R1, (double2*)V, st)) != RR_OK) return s;
   RR_CUDA(cudaMemcpyAsync(sigma_halko, w.sig, (size_t)F * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  RR_CUDA(cudaStreamSynchronize(st));
+  if (fa->sched_mode != SCHED_REPLAY) RR_CUDA(cudaStreamSynchronize(st));
   return conv;
 }
 
@@ -783,7 +952,7 @@ extern "C" rr_status rr_modes(rr_factors* fa, int k, void* V, void* U, double* s
   if ((s = launch_finish_modes(F, N, k, (double2*)U, (double2*)V, sigma, w.W1, w.W3, w.dpart,
                                w.nblk_col, w.rank, w.phase, st)) != RR_OK)
     return s;
-  RR_CUDA(cudaStreamSynchronize(st));
+  if (fa->sched_mode != SCHED_REPLAY) RR_CUDA(cudaStreamSynchronize(st));
   return conv;
 }
 
@@ -826,6 +995,7 @@ extern "C" rr_status rr_gain_grad(rr_factors* fa, int k, int J, const void* U, c
 
 extern "C" rr_status rr_refactor(rr_factors* fa, const double* shifts) {
   if (!fa || !shifts) return arg_error("rr_refactor: null argument");
+  if (fa->is_view) return arg_error("rr_refactor: factors owned by a batch plan");
   const int F = fa->F;
   for (int f = 0; f < 2 * F; ++f)
     if (!std::isfinite(shifts[f])) return arg_error("rr_refactor: shifts must be finite");

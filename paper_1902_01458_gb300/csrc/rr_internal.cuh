@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "rr.h"
 
@@ -132,7 +133,30 @@ struct rr_factors {
   int kmax;
   void* ws;          // one allocation, carved below
   size_t ws_bytes;
+  // A view (batch plans) aliases the factors G and the device shifts of a
+  // parent over a range of its shifts; it owns its staging buffers, flags,
+  // workspace and TMA maps, and never runs the factorisation.
+  int is_view;
+  // Host decisions recorded for graph capture.  SCHED_RECORD runs eagerly and
+  // appends every data-dependent decision (refinement corrections per solve,
+  // shifted CholeskyQR per QR) to sched; SCHED_REPLAY issues the same launch
+  // sequence without host reads, logging residual norms and breakdown flags
+  // into the device check log chk for inspection after the graph has run.
+  int sched_mode;
+  std::vector<int>* sched;      // owned
+  size_t sched_pos;
+  char* chk;                    // device check log (owned), chk_cap bytes
+  size_t chk_cap, chk_off, chk_need;
+  std::vector<long long>* chk_desc;  // owned: (kind, byte offset, count) triples
+  // tuning overrides (0 = built-in choice): K-split of the tensor-core sweep;
+  // 1 = trailing update on the CUDA cores; factor only the first columns
+  int tune_ks;
+  int tune_update;
+  int factor_cols;
 };
+
+enum { SCHED_EAGER = 0, SCHED_RECORD = 1, SCHED_REPLAY = 2 };
+enum { CHK_SOLVE = 0, CHK_CQR = 1 };
 
 // ------------------------------------------------------------ error state
 void set_error(const std::string& msg);
@@ -151,6 +175,13 @@ rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int 
 rr_status launch_residual(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
                           const double2* b, const double2* x, double2* r, cudaStream_t st);
 rr_status launch_phi(const OpDev& d, double* phi, cudaStream_t st);
+
+// rr_api.cu: views over factors and graph-mode helpers of batch plans
+rr_status factors_view(rr_factors* parent, int f0, int nf, cudaStream_t st, rr_factors** out);
+rr_status factor_async(rr_factors* fa);
+rr_status factor_flags(rr_factors* fa);
+rr_status factors_reserve(rr_factors* fa, int k);
+rr_status time_solve(rr_factors* fa, int k, float* ms);
 
 // factor.cu
 rr_status launch_factor(rr_factors* f);
@@ -201,6 +232,12 @@ enum {
   PROF_SCHUR = 0, PROF_PANEL = 1, PROF_ROWBLOCK = 2, PROF_UPDATE = 3, PROF_FINALIZE = 4,
   PROF_SWEEP = 5, PROF_RESIDUAL = 6, PROF_GRAM = 7, PROF_RIGHTMUL = 8, PROF_SMALL = 9,
   PROF_OTHER = 10, PROF_N = 11
+};
+// While a ProfSuspend lives (graph capture), launches are neither counted
+// nor timed.
+struct ProfSuspend {
+  ProfSuspend();
+  ~ProfSuspend();
 };
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);

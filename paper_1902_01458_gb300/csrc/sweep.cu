@@ -737,6 +737,10 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
         const double eff = (double)items / (double)(waves * nsm);
         if (eff > best + 1e-9) { best = eff; KS = ksr; }
       }
+      if (fa->tune_ks > 0) {  // tuned split count (at most the 4 partial buffers)
+        const int cppc = (nch + std::min(fa->tune_ks, 4) - 1) / std::min(fa->tune_ks, 4);
+        KS = (nch + cppc - 1) / cppc;
+      }
       const int cpp = (nch + KS - 1) / KS;
       const int nitems = nrt * F * KS;
       const int grid_x = std::min(nitems, nsm);

@@ -182,3 +182,29 @@ def config_small_ns(nx: int = 24, ny: int = 20, k: int = 8,
     g = ns_grid(nx, ny)
     return Workload(f"ns2d-{nx}x{ny}-k{k}", g, shear_bubble_flow(g),
                     log_omegas(nfreq, 0.3, 3.0), k, 1000, True)
+
+
+@dataclasses.dataclass(frozen=True)
+class BatchProblem:
+    nx: int
+    ny: int
+    k: int
+    omega: float            # shift s = i * omega
+    seed: int               # Omega seed
+
+
+def config_batched(nprob: int = 128, seed: int = 1234,
+                   nx_set=(128, 256, 384), ny_set=(64, 128, 192, 256),
+                   k_set=(8, 16, 32, 64), omega_lo: float = 0.1,
+                   omega_hi: float = 8.0) -> list[BatchProblem]:
+    """Uneven batch: nprob NS problems (q = 3, shear-bubble base flow) with
+    (nx, ny, k) drawn uniformly from the sets and omega ~ U[omega_lo,
+    omega_hi], from one seeded generator; Omega seed of problem i is 1000 + i.
+    The defaults are the 128-problem batching workload."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nprob):
+        out.append(BatchProblem(nx=int(rng.choice(nx_set)), ny=int(rng.choice(ny_set)),
+                                k=int(rng.choice(k_set)),
+                                omega=float(rng.uniform(omega_lo, omega_hi)), seed=1000 + i))
+    return out
