@@ -73,7 +73,16 @@ enum { RR_ADVDIFF_SCALAR = 1, RR_ISO_NS2D = 3 };
  *    linearised about (rho, U, V), p = rho / mach^2, Reynolds number re,
  *    second-order central differences (4-corner cross derivative).
  * Sponge s_s = sponge_max * xi^2 on the outer sponge_frac of each
- * (non-periodic) boundary, xi the normalised depth into the layer. */
+ * (non-periodic) boundary, xi the normalised depth into the layer.
+ * Boundary closure per side (Sec. III.A: Dirichlet velocities and Neumann
+ * pressure at the far field, Neumann for every variable at the outlet):
+ * neumann[side] is a bit mask over the q variables (bit c = variable c,
+ * in the order rho', u', v'), sides x0, x1, y0, y1.  A set bit makes the
+ * ghost node of that variable equal to the adjacent interior node (the
+ * coefficient folds onto it); a clear bit keeps the zero (Dirichlet) ghost.
+ * All zero is the homogeneous Dirichlet operator; the paper's closure for
+ * RR_ISO_NS2D is {1, 7, 1, 1} (p' = rho'/mach^2, so Neumann pressure is
+ * Neumann rho').  The y masks must be zero when periodic_y is set. */
 typedef struct {
   int kind;
   int nx, ny;
@@ -83,6 +92,7 @@ typedef struct {
   double mach;
   double sponge_max;
   double sponge_frac;
+  int neumann[4];
 } rr_grid;
 
 /* Base-flow fields on the interior nodes, host pointers to nx*ny doubles
@@ -338,7 +348,10 @@ typedef struct {
   int graph_nodes;        /* nodes of the graph                             */
   int kernel_nodes;       /* kernel launches per rr_batch_run               */
   int cuda_core_updates;  /* groups tuned to the CUDA-core trailing update  */
-  double plan_ms;         /* host wall time of rr_batch_create              */
+  double plan_ms;         /* host wall time of rr_batch_create, of which:   */
+  double calib_ms;        /*   calibration (eager factor + Algorithm 1)     */
+  double tune_ms;         /*   kernel and lane tuning                       */
+  double capture_ms;      /*   final capture + instantiation               */
   double tuned_ms;        /* best whole-graph time seen by the lane tuner   */
 } rr_batch_desc;
 

@@ -17,7 +17,10 @@ follow the reading fixed for this project:
 
 Discretisation: 2nd-order central differences on nx x ny interior nodes with
 homogeneous Dirichlet ghost nodes (or periodic y); the cross derivative is
-the 4-corner stencil.  Derivatives of the base flow use the same central
+the 4-corner stencil.  Optionally (Sec. III.A's far-field / outlet closure)
+a variable's ghost node on a side equals the adjacent interior node
+(Neumann); grid.neumann holds the variable bit masks of the sides x0, x1,
+y0, y1, and each variable gets difference matrices with its own closure.  Derivatives of the base flow use the same central
 differences and first-order one-sided differences at the first/last node
 (second derivatives reuse the neighbouring node's 3-point stencil there).
 
@@ -31,24 +34,36 @@ import scipy.sparse as sp
 
 
 # ----------------------------------------------------------------- 1-D pieces
-def d1_unknown(n: int, h: float, periodic: bool = False) -> sp.csr_matrix:
-    """Central first difference acting on unknowns with zero ghost values."""
+def d1_unknown(n: int, h: float, periodic: bool = False, neu_lo: bool = False,
+               neu_hi: bool = False) -> sp.csr_matrix:
+    """Central first difference acting on unknowns; the ghost value beyond
+    each end is zero, or (neu_lo / neu_hi) the end node's own value."""
     e = np.ones(n)
     m = sp.diags([-e[:-1], e[:-1]], [-1, 1], shape=(n, n), format="lil")
     if periodic:
         m[0, n - 1] = -1.0
         m[n - 1, 0] = 1.0
+    if neu_lo:   # (u_1 - u_ghost) with u_ghost = u_0
+        m[0, 0] += -1.0
+    if neu_hi:   # (u_ghost - u_{n-2}) with u_ghost = u_{n-1}
+        m[n - 1, n - 1] += 1.0
     return (m / (2.0 * h)).tocsr()
 
 
-def d2_unknown(n: int, h: float, periodic: bool = False) -> sp.csr_matrix:
-    """3-point second difference acting on unknowns with zero ghost values."""
+def d2_unknown(n: int, h: float, periodic: bool = False, neu_lo: bool = False,
+               neu_hi: bool = False) -> sp.csr_matrix:
+    """3-point second difference acting on unknowns; ghost values as in
+    d1_unknown."""
     e = np.ones(n)
     m = sp.diags([e[:-1], -2.0 * e, e[:-1]], [-1, 0, 1], shape=(n, n),
                  format="lil")
     if periodic:
         m[0, n - 1] = 1.0
         m[n - 1, 0] = 1.0
+    if neu_lo:
+        m[0, 0] += 1.0
+    if neu_hi:
+        m[n - 1, n - 1] += 1.0
     return (m / (h * h)).tocsr()
 
 
@@ -130,18 +145,31 @@ def sponge(grid) -> np.ndarray:
 
 
 # --------------------------------------------------------------- assembly
-def assemble(grid, flow) -> sp.csr_matrix:
-    """Sparse L (N x N, real) for the grid kind, unknown order ((ix*ny)+iy)*q+c."""
+def variable_operators(grid, var: int) -> dict:
+    """Difference matrices (nx*ny square) acting on variable `var`, with that
+    variable's closure on each side."""
     nx, ny = grid.nx, grid.ny
+    masks = getattr(grid, "neumann", (0, 0, 0, 0))
+    x0, x1, y0, y1 = (bool((int(m) >> var) & 1) for m in masks)
     Ix = sp.identity(nx, format="csr")
     Iy = sp.identity(ny, format="csr")
-    Dx = sp.kron(d1_unknown(nx, grid.dx), Iy, format="csr")
-    Dy = sp.kron(Ix, d1_unknown(ny, grid.dy, grid.periodic_y), format="csr")
-    Dxx = sp.kron(d2_unknown(nx, grid.dx), Iy, format="csr")
-    Dyy = sp.kron(Ix, d2_unknown(ny, grid.dy, grid.periodic_y), format="csr")
-    Dxy = sp.kron(d1_unknown(nx, grid.dx),
-                  d1_unknown(ny, grid.dy, grid.periodic_y), format="csr")
-    lap = Dxx + Dyy
+    d1x = d1_unknown(nx, grid.dx, False, x0, x1)
+    d1y = d1_unknown(ny, grid.dy, grid.periodic_y, y0, y1)
+    ops = {
+        "Dx": sp.kron(d1x, Iy, format="csr"),
+        "Dy": sp.kron(Ix, d1y, format="csr"),
+        "Dxx": sp.kron(d2_unknown(nx, grid.dx, False, x0, x1), Iy, format="csr"),
+        "Dyy": sp.kron(Ix, d2_unknown(ny, grid.dy, grid.periodic_y, y0, y1), format="csr"),
+        "Dxy": sp.kron(d1x, d1y, format="csr"),
+    }
+    ops["lap"] = ops["Dxx"] + ops["Dyy"]
+    return ops
+
+
+def assemble(grid, flow) -> sp.csr_matrix:
+    """Sparse L (N x N, real) for the grid kind, unknown order ((ix*ny)+iy)*q+c."""
+    ops = [variable_operators(grid, v) for v in range(grid.q)]
+    lap = ops[0]["lap"]
 
     def dg(a):
         return sp.diags(np.asarray(a, dtype=np.float64).ravel(), 0,
@@ -149,11 +177,13 @@ def assemble(grid, flow) -> sp.csr_matrix:
 
     U, V, R = flow.u, flow.v, flow.rho
     sig = sponge(grid)
-    adv = -(dg(U) @ Dx + dg(V) @ Dy)
+
+    def adv(v):  # -(U d_x + V d_y) acting on variable v
+        return -(dg(U) @ ops[v]["Dx"] + dg(V) @ ops[v]["Dy"])
 
     if grid.q == 1:
         nu = 1.0 / grid.re
-        return (adv + nu * lap - dg(sig)).tocsr()
+        return (adv(0) + nu * lap - dg(sig)).tocsr()
 
     c2 = 1.0 / grid.mach ** 2
     re = grid.re
@@ -166,18 +196,20 @@ def assemble(grid, flow) -> sp.csr_matrix:
     fu = (dU["xx"] + dU["yy"] + (dU["xx"] + dV["xy"]) / 3.0) / re
     fv = (dV["xx"] + dV["yy"] + (dU["xy"] + dV["yy"]) / 3.0) / re
 
+    # blk[a][b]: equation a acting on variable b (b's difference matrices)
+    o0, o1, o2 = ops
     blk = [[None] * 3 for _ in range(3)]
-    blk[0][0] = adv - dg(divU) - dg(sig)
-    blk[0][1] = -dg(dR["x"]) - dg(R) @ Dx
-    blk[0][2] = -dg(dR["y"]) - dg(R) @ Dy
-    blk[1][0] = (-c2 * dg(1.0 / R) @ Dx + c2 * dg(dR["x"] / R ** 2)
+    blk[0][0] = adv(0) - dg(divU) - dg(sig)
+    blk[0][1] = -dg(dR["x"]) - dg(R) @ o1["Dx"]
+    blk[0][2] = -dg(dR["y"]) - dg(R) @ o2["Dy"]
+    blk[1][0] = (-c2 * dg(1.0 / R) @ o0["Dx"] + c2 * dg(dR["x"] / R ** 2)
                  - dg(fu / R ** 2))
-    blk[1][1] = adv - dg(dU["x"]) + visc @ (lap + Dxx / 3.0) - dg(sig)
-    blk[1][2] = -dg(dU["y"]) + visc @ (Dxy / 3.0)
-    blk[2][0] = (-c2 * dg(1.0 / R) @ Dy + c2 * dg(dR["y"] / R ** 2)
+    blk[1][1] = adv(1) - dg(dU["x"]) + visc @ (o1["lap"] + o1["Dxx"] / 3.0) - dg(sig)
+    blk[1][2] = -dg(dU["y"]) + visc @ (o2["Dxy"] / 3.0)
+    blk[2][0] = (-c2 * dg(1.0 / R) @ o0["Dy"] + c2 * dg(dR["y"] / R ** 2)
                  - dg(fv / R ** 2))
-    blk[2][1] = -dg(dV["x"]) + visc @ (Dxy / 3.0)
-    blk[2][2] = adv - dg(dV["y"]) + visc @ (lap + Dyy / 3.0) - dg(sig)
+    blk[2][1] = -dg(dV["x"]) + visc @ (o1["Dxy"] / 3.0)
+    blk[2][2] = adv(2) - dg(dV["y"]) + visc @ (o2["lap"] + o2["Dyy"] / 3.0) - dg(sig)
 
     L = None
     for a in range(3):

@@ -37,7 +37,7 @@ class rr_grid(ctypes.Structure):
                 ("x1", ctypes.c_double), ("y0", ctypes.c_double),
                 ("y1", ctypes.c_double), ("re", ctypes.c_double),
                 ("mach", ctypes.c_double), ("sponge_max", ctypes.c_double),
-                ("sponge_frac", ctypes.c_double)]
+                ("sponge_frac", ctypes.c_double), ("neumann", ctypes.c_int * 4)]
 
 
 class rr_baseflow(ctypes.Structure):
@@ -79,7 +79,8 @@ class rr_batch_desc(ctypes.Structure):
     _fields_ = [("groups", ctypes.c_int), ("views", ctypes.c_int), ("lanes", ctypes.c_int),
                 ("graph_nodes", ctypes.c_int), ("kernel_nodes", ctypes.c_int),
                 ("cuda_core_updates", ctypes.c_int), ("plan_ms", ctypes.c_double),
-                ("tuned_ms", ctypes.c_double)]
+                ("calib_ms", ctypes.c_double), ("tune_ms", ctypes.c_double),
+                ("capture_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -185,7 +186,8 @@ def rr_create_operator(grid, rho, u, v, weights=None, device: int = 0):
                 float(grid.x0), float(grid.x1), float(grid.y0), float(grid.y1),
                 float(grid.re), float(getattr(grid, "mach", 0.0)),
                 float(getattr(grid, "sponge_max", 0.0)),
-                float(getattr(grid, "sponge_frac", 0.1)))
+                float(getattr(grid, "sponge_frac", 0.1)),
+                (ctypes.c_int * 4)(*[int(m) for m in getattr(grid, "neumann", (0, 0, 0, 0))]))
     keep = []
 
     def arr(a):

@@ -30,42 +30,58 @@ constexpr int PANEL_THREADS = 512;
 
 __device__ __forceinline__ int slotx(int dx, int dy) { return (dx + 1) * 3 + (dy + 1); }
 
-// M = D_i (+ L_{i,i-1} X_{i-1} for i > 0), i.e. S_i = D_i - A_i X_{i-1}.
+// M = D_i (+ L_{i,i-1} X_{i-1} for i > 0), i.e. S_i = D_i - A_i X_{i-1}.  One
+// CTA per (SCHUR_ROWS rows, problem): a row's stencil coefficients are read
+// once (uniform loads) and its columns are spread over the threads.
+constexpr int SCHUR_ROWS = 4, SCHUR_THREADS = 256;
 template <typename T>
-__global__ void schur_kernel(OpView op, const double2* __restrict__ shifts, int i,
-                             const C_t<T>* __restrict__ Xprev, size_t xstride,
-                             C_t<T>* __restrict__ M) {
+__global__ void __launch_bounds__(SCHUR_THREADS)
+schur_kernel(OpView op, const double2* __restrict__ shifts, int i,
+             const C_t<T>* __restrict__ Xprev, size_t xstride, C_t<T>* __restrict__ M) {
   using C = C_t<T>;
   const int b = op.b, q = op.q;
-  const int r = blockIdx.y;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int f = blockIdx.z;
-  if (c >= b) return;
-  const int iy = r / q;
-  const size_t nrow = (size_t)i * b + r;
-  const double* cf = op.coef + nrow * op.S;
-  C val = czero<C>();
-  if (r == c) val = mk((T)shifts[f].x, (T)shifts[f].y);
-  for (int dy = -1; dy <= 1; ++dy) {
-    int jy = nbr_y(iy, dy, op.ny, op.periodic);
-    if (jy < 0) continue;
-    for (int cp = 0; cp < q; ++cp) {
-      int m = jy * q + cp;
-      if (m == c) val.x -= (T)cf[slotx(0, dy) * q + cp];
-    }
-  }
-  if (i > 0) {
-    const C* Xp = Xprev + (size_t)f * xstride;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int jy = nbr_y(iy, dy, op.ny, op.periodic);
-      if (jy < 0) continue;
-      for (int cp = 0; cp < q; ++cp) {
-        T a = (T)cf[slotx(-1, dy) * q + cp];
-        if (a != (T)0) val = crfma(a, Xp[(size_t)(jy * q + cp) * b + c], val);
+  const int f = blockIdx.y;
+  const C sh = mk((T)shifts[f].x, (T)shifts[f].y);
+  const C* Xp = Xprev ? Xprev + (size_t)f * xstride : nullptr;
+  C* Mf = M + (size_t)f * b * b;
+  for (int rr = 0; rr < SCHUR_ROWS; ++rr) {
+    const int r = blockIdx.x * SCHUR_ROWS + rr;
+    if (r >= b) break;
+    const int iy = r / q;
+    const size_t cf = ((size_t)i * b + r) * op.S;
+    // D_i entries (x-offset 0) and A_i entries (x-offset -1) of row r: three
+    // neighbours in y times q <= 3 components
+    // (entry t = (dy + 1) * q + cp; unrolled so the arrays stay in registers)
+    int cols[9];
+    T dval[9], aval[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      cols[t] = -1;
+      dval[t] = aval[t] = (T)0;
+      if (t < 3 * q) {
+        const int dy = t / q - 1, cp = t - (t / q) * q;
+        const int jy = nbr_y(iy, dy, op.ny, op.periodic);
+        if (jy >= 0) {
+          cols[t] = jy * q + cp;
+          dval[t] = coefv<T>(op, cf + slotx(0, dy) * q + cp);
+          aval[t] = coefv<T>(op, cf + slotx(-1, dy) * q + cp);
+        }
       }
     }
+    for (int c = threadIdx.x; c < b; c += SCHUR_THREADS) {
+      C val = (r == c) ? sh : czero<C>();
+#pragma unroll
+      for (int t = 0; t < 9; ++t)
+        if (cols[t] == c) val.x -= dval[t];
+      if (Xp) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+          if (cols[t] >= 0 && aval[t] != (T)0)
+            val = crfma(aval[t], Xp[(size_t)cols[t] * b + c], val);
+      }
+      Mf[(size_t)r * b + c] = val;
+    }
   }
-  M[(size_t)f * b * b + (size_t)r * b + c] = val;
 }
 
 // argmax reduction helper: larger value wins, lower index on ties
@@ -217,24 +233,45 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
     if (lane == 0) s_nk = cnt;
   }
 
-  // inverses of U11 and of the unit lower L11 (rows = chosen slots in order),
-  // then T^{-1} = U11^{-1} L11^{-1}
-  if (tid < nbk) {
-    const int c = tid;
-    for (int i = 0; i < NB; ++i) { Ui[i][c] = czero<C>(); Li[i][c] = czero<C>(); }
-    for (int i = c; i >= 0; --i) {
-      const C* row = P + chosen[i] * PS;
-      C s = (i == c) ? mk((T)1, (T)0) : czero<C>();
-      for (int m = i + 1; m <= c; ++m) s = csub(s, cmul(row[m], Ui[m][c]));
-      Ui[i][c] = cmul(s, cinv(row[i]));
+  // inverses of U11 (warp 0) and of the unit lower L11 (warp 1), rows =
+  // chosen slots in order, one column per lane held in registers; then
+  // T^{-1} = U11^{-1} L11^{-1}
+  if (warp == 0 && lane < nbk) {
+    const int c = lane;
+    C u[NB];
+#pragma unroll
+    for (int i = NB - 1; i >= 0; --i) {
+      u[i] = czero<C>();
+      if (i <= c) {
+        const C* row = P + chosen[i] * PS;
+        C sacc = (i == c) ? mk((T)1, (T)0) : czero<C>();
+#pragma unroll
+        for (int m = i + 1; m < NB; ++m)
+          if (m <= c) sacc = csub(sacc, cmul(row[m], u[m]));
+        u[i] = cmul(sacc, cinv(row[i]));
+      }
     }
-    Li[c][c] = mk((T)1, (T)0);
-    for (int i = c + 1; i < nbk; ++i) {
-      const C* row = P + chosen[i] * PS;
-      C s = czero<C>();
-      for (int m = c; m < i; ++m) s = csub(s, cmul(row[m], Li[m][c]));
-      Li[i][c] = s;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) Ui[i][c] = u[i];
+  } else if (warp == 1 && lane < nbk) {
+    const int c = lane;
+    C l[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      l[i] = czero<C>();
+      if (i == c) {
+        l[i] = mk((T)1, (T)0);
+      } else if (i > c && i < nbk) {
+        const C* row = P + chosen[i] * PS;
+        C sacc = czero<C>();
+#pragma unroll
+        for (int m = 0; m < i; ++m)
+          if (m >= c) sacc = csub(sacc, cmul(row[m], l[m]));
+        l[i] = sacc;
+      }
     }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) Li[i][c] = l[i];
   }
   __syncthreads();
   for (int e = tid; e < nbk * nbk; e += nt) {
@@ -744,7 +781,7 @@ __global__ void gj_finalize_kernel(OpView op, int i, int RB, const C_t<T>* __res
       if (iym < 0) continue;
       for (int cm = 0; cm < q; ++cm) {
         int m = iym * q + cm;
-        T a = (T)op.coef[((size_t)i * b + m) * op.S + slotx(1, dy) * q + cc];
+        T a = coefv<T>(op, ((size_t)i * b + m) * op.S + slotx(1, dy) * q + cc);
         if (a != (T)0) s = crfma(a, Gs[rr * b + m], s);
       }
     }
@@ -843,10 +880,10 @@ rr_status factor_impl(rr_factors* fa) {
   for (int i = 0; i < ncols; ++i) {
     iota_kernel<<<(b * F + 255) / 256, 256, 0, st>>>(fa->perm, b, F);
     prof_count(1);
-    dim3 gs((b + 127) / 128, b, F);
+    dim3 gs((b + SCHUR_ROWS - 1) / SCHUR_ROWS, F);
     const C* Xprev = (i > 0) ? X : nullptr;
     prof_begin(PROF_SCHUR, st);
-    schur_kernel<T><<<gs, 128, 0, st>>>(ov, fa->shifts, i, Xprev, xstride, M);
+    schur_kernel<T><<<gs, SCHUR_THREADS, 0, st>>>(ov, fa->shifts, i, Xprev, xstride, M);
     prof_end(PROF_SCHUR, st);
     panel(0, st);
     for (int p = 0; p < P; ++p) {

@@ -21,6 +21,7 @@ namespace {
 struct GradParams {
   int kind, q, nx, ny, periodic, npts;
   double dx, dy, re, c2;
+  int neu[4];  // Neumann variable masks of the sides x0, x1, y0, y1
 };
 
 // local base-flow quantities per field: value, d/dx, d/dy, d2/dx2, d2/dy2, d2/dxdy
@@ -39,12 +40,21 @@ __global__ void grad_local_kernel(GradParams p, const double* __restrict__ flow,
   const int pt = blockIdx.x * blockDim.x + threadIdx.x;
   if (pt >= p.npts) return;
   const int i = pt / p.ny, j = pt % p.ny, q = p.q;
-  int nb[9];
+  // neighbour point of every slot for every variable: -1 for a Dirichlet
+  // ghost, the adjacent interior point for a Neumann ghost (the closure of
+  // the assembly)
+  int nb[3][9];
   for (int dxo = -1; dxo <= 1; ++dxo)
     for (int dyo = -1; dyo <= 1; ++dyo) {
-      int jx = i + dxo;
-      int jy = nbr_y(j, dyo, p.ny, p.periodic);
-      nb[slot(dxo, dyo)] = (jx >= 0 && jx < p.nx && jy >= 0) ? jx * p.ny + jy : -1;
+      const int jx = i + dxo;
+      const int jy = nbr_y(j, dyo, p.ny, p.periodic);
+      const bool gx = jx < 0 || jx >= p.nx, gy = jy < 0;
+      const int mx = gx ? p.neu[jx < 0 ? 0 : 1] : ~0;
+      const int my = gy ? p.neu[j + dyo < 0 ? 2 : 3] : ~0;
+      for (int in = 0; in < q; ++in) {
+        const bool keep = ((mx >> in) & 1) && ((my >> in) & 1);
+        nb[in][slot(dxo, dyo)] = keep ? (gx ? i : jx) * p.ny + (gy ? j : jy) : -1;
+      }
     }
   const double hx = 1.0 / (2.0 * p.dx), hy = 1.0 / (2.0 * p.dy);
   const double ixx = 1.0 / (p.dx * p.dx), iyy = 1.0 / (p.dy * p.dy);
@@ -59,8 +69,8 @@ __global__ void grad_local_kernel(GradParams p, const double* __restrict__ flow,
       const int n = pt * q + o;
       for (int s = 0; s < 9; ++s) {
         double acc = 0.0;
-        if (nb[s] >= 0) {
-          const int m = nb[s] * q + in;
+        if (nb[in][s] >= 0) {
+          const int m = nb[in][s] * q + in;
           for (int f = 0; f < F; ++f) {
             const double2* Af = A + ((size_t)f * N + n) * J;
             const double2* Bf = B + ((size_t)f * N + m) * J;
@@ -259,6 +269,7 @@ rr_status launch_gain_grad(const OpDev& d, const rr_grid& g, int F, int J, const
   p.npts = d.nx * d.ny;
   p.dx = d.dx; p.dy = d.dy; p.re = g.re;
   p.c2 = d.kind == RR_ISO_NS2D ? 1.0 / (g.mach * g.mach) : 0.0;
+  for (int e = 0; e < 4; ++e) p.neu[e] = g.neumann[e];
   prof_count(2);
   grad_local_kernel<<<(p.npts + 127) / 128, 128, 0, st>>>(p, d.flow, F, J, d.n, A, B, sigma,
                                                           sstride, featbar);

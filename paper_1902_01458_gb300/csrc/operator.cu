@@ -49,6 +49,7 @@ struct Field {
 struct AsmParams {
   int kind, q, nx, ny, periodic;
   double dx, dy, x0, x1, y0, y1, re, c2, smax, sfrac;
+  int neu[4];  // Neumann variable masks of the sides x0, x1, y0, y1
 };
 
 __device__ double sponge_at(const AsmParams& p, int i, int j) {
@@ -156,13 +157,24 @@ __global__ void assemble_kernel(AsmParams p, const double* __restrict__ flow,
     addDiag(2, 2, -Vy - sg);
   }
 
+  // boundary closure: a ghost neighbour of variable b is zero (Dirichlet) or,
+  // where b's bit is set on every side the ghost lies beyond, equal to the
+  // adjacent interior node, so its coefficient moves to that node's slot
   for (int dxo = -1; dxo <= 1; ++dxo)
     for (int dyo = -1; dyo <= 1; ++dyo) {
-      bool ok = (i + dxo >= 0 && i + dxo < p.nx) &&
-                (p.periodic || (j + dyo >= 0 && j + dyo < p.ny));
-      if (!ok)
-        for (int a = 0; a < q; ++a)
-          for (int b = 0; b < q; ++b) c[a][slot(dxo, dyo)][b] = 0.0;
+      const bool gx = i + dxo < 0 || i + dxo >= p.nx;
+      const bool gy = !p.periodic && (j + dyo < 0 || j + dyo >= p.ny);
+      if (!gx && !gy) continue;
+      const int mx = gx ? p.neu[i + dxo < 0 ? 0 : 1] : ~0;
+      const int my = gy ? p.neu[j + dyo < 0 ? 2 : 3] : ~0;
+      const int to = slot(gx ? 0 : dxo, gy ? 0 : dyo);
+      for (int b = 0; b < q; ++b) {
+        const bool fold = ((mx >> b) & 1) && ((my >> b) & 1);
+        for (int a = 0; a < q; ++a) {
+          if (fold) c[a][to][b] += c[a][slot(dxo, dyo)][b];
+          c[a][slot(dxo, dyo)][b] = 0.0;
+        }
+      }
     }
   for (int a = 0; a < q; ++a) {
     double* out = coef + (size_t)(pt * q + a) * S;
@@ -258,16 +270,29 @@ __global__ void phi_kernel(const double* __restrict__ flow, int nx, int ny, int 
 
 }  // namespace
 
+__global__ void round_coef_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
+}
+
 rr_status launch_assemble(OpDev& d, const rr_grid& g, cudaStream_t st) {
   AsmParams p;
   p.kind = g.kind; p.q = d.q; p.nx = d.nx; p.ny = d.ny; p.periodic = d.periodic;
   p.dx = d.dx; p.dy = d.dy; p.x0 = g.x0; p.x1 = g.x1; p.y0 = g.y0; p.y1 = g.y1;
   p.re = g.re; p.c2 = (g.kind == RR_ISO_NS2D) ? 1.0 / (g.mach * g.mach) : 0.0;
   p.smax = g.sponge_max; p.sfrac = g.sponge_frac;
+  for (int e = 0; e < 4; ++e) p.neu[e] = g.neumann[e];
   int npts = d.nx * d.ny;
   prof_count(1);
   assemble_kernel<<<(npts + 127) / 128, 128, 0, st>>>(p, d.flow, d.coef);
   RR_CUDA(cudaGetLastError());
+  if (d.coef32) {
+    const size_t n = (size_t)d.n * 9 * d.q;
+    prof_count(1);
+    round_coef_kernel<<<(int)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(d.coef, d.coef32, n);
+    RR_CUDA(cudaGetLastError());
+  }
   return RR_OK;
 }
 

@@ -459,6 +459,11 @@ extern "C" rr_status rr_create_operator(const rr_grid* g, const rr_baseflow* fl,
   if (!(g->x1 > g->x0) || !(g->y1 > g->y0)) return arg_error("rr_create_operator: empty domain");
   if (g->sponge_max != 0.0 && !(g->sponge_frac > 0.0 && g->sponge_frac <= 0.5))
     return arg_error("rr_create_operator: sponge_frac must be in (0, 0.5]");
+  for (int e = 0; e < 4; ++e)
+    if (g->neumann[e] < 0 || g->neumann[e] >= (1 << g->kind))
+      return arg_error("rr_create_operator: neumann masks must be bit masks over the q variables");
+  if (g->periodic_y && (g->neumann[2] || g->neumann[3]))
+    return arg_error("rr_create_operator: a periodic y direction has no y boundary closure");
   if (!fl->u || !fl->v || (g->kind == RR_ISO_NS2D && !fl->rho))
     return arg_error("rr_create_operator: missing base-flow field");
   const size_t npts = (size_t)g->nx * g->ny;
@@ -484,14 +489,15 @@ extern "C" rr_status rr_create_operator(const rr_grid* g, const rr_baseflow* fl,
   d.dx = (g->x1 - g->x0) / (g->nx + 1);
   d.dy = d.periodic ? (g->y1 - g->y0) / g->ny : (g->y1 - g->y0) / (g->ny + 1);
   d.device = device;
-  d.coef = nullptr; d.wsqrt = nullptr; d.wisqrt = nullptr; d.flow = nullptr;
+  d.coef = nullptr; d.coef32 = nullptr; d.wsqrt = nullptr; d.wisqrt = nullptr; d.flow = nullptr;
   rr_status s;
   auto fail = [&](rr_status st) {
-    cudaFree(d.coef); cudaFree(d.wsqrt); cudaFree(d.wisqrt); cudaFree(d.flow);
+    cudaFree(d.coef); cudaFree(d.coef32); cudaFree(d.wsqrt); cudaFree(d.wisqrt); cudaFree(d.flow);
     delete op;
     return st;
   };
   if ((s = dalloc(&d.coef, N * 9 * q * sizeof(double))) != RR_OK) return fail(s);
+  if ((s = dalloc(&d.coef32, N * 9 * q * sizeof(float))) != RR_OK) return fail(s);
   if ((s = dalloc(&d.flow, 3 * npts * sizeof(double))) != RR_OK) return fail(s);
   std::vector<double> hf(3 * npts, 1.0);
   if (fl->rho) std::memcpy(hf.data(), fl->rho, npts * sizeof(double));
@@ -525,6 +531,7 @@ extern "C" rr_status rr_destroy_operator(rr_operator* op) {
   if (!op) return RR_OK;
   DeviceGuard guard(op->d.device);
   cudaFree(op->d.coef);
+  cudaFree(op->d.coef32);
   cudaFree(op->d.wsqrt);
   cudaFree(op->d.wisqrt);
   cudaFree(op->d.flow);

@@ -73,6 +73,7 @@ template <> __device__ __forceinline__ double2 ccast<double2, float2>(float2 a) 
 struct OpDev {
   int kind, q, nx, ny, b, n, periodic;
   double* coef;      // [N][9q]
+  float* coef32;     // [N][9q] the same coefficients rounded once to FP32 (FP32 factors)
   double* wsqrt;     // [N] W^{1/2} or nullptr (identity)
   double* wisqrt;    // [N] W^{-1/2} or nullptr
   double* flow;      // [3][nx*ny] rho, U, V
@@ -88,15 +89,28 @@ struct rr_operator {
 // Device-side view of the operator passed by value to kernels.
 struct OpView {
   const double* coef;
+  const float* coef32;
   int q, nx, ny, b, n, periodic, S;
 };
 
 inline OpView view(const OpDev& d) {
   OpView v;
   v.coef = d.coef;
+  v.coef32 = d.coef32;
   v.q = d.q; v.nx = d.nx; v.ny = d.ny; v.b = d.b; v.n = d.n;
   v.periodic = d.periodic; v.S = 9 * d.q;
   return v;
+}
+
+// Stencil coefficient in the arithmetic of T: FP64 kernels read the FP64
+// array, FP32 kernels its copy rounded once at assembly (the same value a
+// conversion at every use would give).
+template <typename T> __device__ __forceinline__ T coefv(const OpView& op, size_t idx);
+template <> __device__ __forceinline__ double coefv<double>(const OpView& op, size_t idx) {
+  return op.coef[idx];
+}
+template <> __device__ __forceinline__ float coefv<float>(const OpView& op, size_t idx) {
+  return op.coef32[idx];
 }
 
 // y index of a neighbour; returns -1 for a Dirichlet ghost.

@@ -52,23 +52,23 @@ __global__ void sweep_rhs_kernel(OpView op, int i, int k, const C_t<T>* in, cons
     if (MODE == FWD) {
       v = in[(size_t)f * NK + row * k + j];
       int iy = m / q;
-      const double* cf = op.coef + row * op.S;
+      const size_t cf = row * op.S;
       for (int dy = -1; dy <= 1; ++dy) {
         int jy = nbr_y(iy, dy, op.ny, op.periodic);
         if (jy < 0) continue;
         for (int cp = 0; cp < q; ++cp) {
-          T a = (T)cf[slotv(-1, dy) * q + cp];
+          T a = coefv<T>(op, cf + slotv(-1, dy) * q + cp);
           if (a != (T)0) v = crfma(a, outf[((size_t)(i - 1) * b + jy * q + cp) * k + j], v);
         }
       }
     } else if (MODE == BWD) {
       int iy = m / q;
-      const double* cf = op.coef + row * op.S;
+      const size_t cf = row * op.S;
       for (int dy = -1; dy <= 1; ++dy) {
         int jy = nbr_y(iy, dy, op.ny, op.periodic);
         if (jy < 0) continue;
         for (int cp = 0; cp < q; ++cp) {
-          T a = (T)cf[slotv(1, dy) * q + cp];
+          T a = coefv<T>(op, cf + slotv(1, dy) * q + cp);
           if (a != (T)0) v = crfma(-a, outf[((size_t)(i + 1) * b + jy * q + cp) * k + j], v);
         }
       }
@@ -80,7 +80,7 @@ __global__ void sweep_rhs_kernel(OpView op, int i, int k, const C_t<T>* in, cons
         if (iyr < 0) continue;
         for (int cr = 0; cr < q; ++cr) {
           size_t rrow = (size_t)(i + 1) * b + iyr * q + cr;
-          T a = (T)op.coef[rrow * op.S + slotv(-1, dy) * q + cm];
+          T a = coefv<T>(op, rrow * op.S + slotv(-1, dy) * q + cm);
           if (a != (T)0) v = crfma(a, outf[rrow * k + j], v);
         }
       }
@@ -111,7 +111,7 @@ __global__ void adj_couple_kernel(OpView op, int i, int k, const C_t<T>* __restr
       if (iym < 0) continue;
       for (int cm = 0; cm < q; ++cm) {
         int m = iym * q + cm;
-        T a = (T)op.coef[((size_t)i * b + m) * op.S + slotv(1, dy) * q + cc];
+        T a = coefv<T>(op, ((size_t)i * b + m) * op.S + slotv(1, dy) * q + cc);
         if (a != (T)0) v = crfma(a, tf[(size_t)m * k + j], v);
       }
     }

@@ -37,7 +37,11 @@ def _cases():
     per = W.Grid(kind=W.KIND_ADVDIFF, nx=6, ny=5, x0=0, x1=2, y0=0, y1=3, re=5.0,
                  periodic_y=True)
     nsp = dataclasses.replace(W.ns_grid(6, 4), re=80.0, periodic_y=True, sponge_max=0.0)
+    nsn = dataclasses.replace(W.ns_grid(7, 6, neumann=W.PAPER_NEUMANN), re=50.0)
+    adn = dataclasses.replace(ad, neumann=(1, 1, 0, 1))
     return [("ns", ns, W.smooth_random_flow(ns, 3, amp=0.2), None),
+            ("ns-neumann", nsn, W.smooth_random_flow(nsn, 8, amp=0.2), None),
+            ("advdiff-neumann", adn, W.smooth_random_flow(adn, 9, amp=0.3), None),
             ("ns-weighted", ns, W.smooth_random_flow(ns, 4, amp=0.2), "w"),
             ("ns-periodic", nsp, W.smooth_random_flow(nsp, 6, amp=0.2), None),
             ("advdiff", ad, W.smooth_random_flow(ad, 5, amp=0.3), None),

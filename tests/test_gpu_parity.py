@@ -32,6 +32,10 @@ def _cases():
         ("ns-random-13x9", W.ns_grid(13, 9), "random"),
         ("advdiff-32x32", W.config_tiny().grid, None),
         ("advdiff-periodic", g1, "vconst"),
+        # Sec. III.A's closure: Neumann rho' at the far field, all at the outlet
+        ("ns-neumann-9x11", W.ns_grid(9, 11, neumann=W.PAPER_NEUMANN), "random"),
+        ("advdiff-neumann-all", W.Grid(kind=W.KIND_ADVDIFF, nx=8, ny=9, x0=0, x1=2, y0=0,
+                                       y1=3, re=5.0, neumann=(1, 1, 1, 1)), "random"),
     ]
 
 
@@ -93,6 +97,8 @@ SOLVE_CASES = [
     ("ns-5x88-ragged-tc-update", lambda: W.ns_grid(5, 88), "random"),
     ("advdiff-periodic", lambda: W.Grid(kind=W.KIND_ADVDIFF, nx=9, ny=12, x0=0, x1=2,
                                         y0=0, y1=3, re=5.0, periodic_y=True), "vconst"),
+    # Neumann closure, b = 144 (tensor-core update and sweeps)
+    ("ns-neumann-6x48", lambda: W.ns_grid(6, 48, neumann=W.PAPER_NEUMANN), "random"),
 ]
 
 
@@ -269,3 +275,37 @@ def test_tensor_core_sweeps_match_cuda_core_sweeps(env, grid_shape, k, adjoint):
         A = op.shifted(L, s).toarray()
         want = np.linalg.solve(A.conj().T if adjoint else A, b[f])
         assert rel_err(xs["fp32"][f], want) < 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_algorithm1_with_neumann_closure_matches_oracle(env, precision):
+    """Sec. III.A's boundary closure (Neumann rho' at the far field, every
+    variable at the outlet) end to end."""
+    torch, rr = env
+    g = W.ns_grid(16, 44, neumann=W.PAPER_NEUMANN)
+    flow = W.shear_bubble_flow(g)
+    L = op.assemble(g, flow)
+    phi = op.phi(g, flow)
+    o = rr.Operator(g, flow)
+    shifts = 1j * np.array([0.35, 2.2])
+    seeds = [77, 78]
+    fa = o.factor(shifts, precision)
+    res = fa.randomized_resolvent(6, seeds, phi=to_dev(phi, torch))
+    tol = 1e-9 if precision == "fp64" else 1e-6
+    for f, s in enumerate(shifts):
+        ref = rs.randomized(L, s, 6, seeds[f], phi=phi)
+        np.testing.assert_allclose(res.sigma.cpu().numpy()[f], ref.sigma, rtol=tol)
+        np.testing.assert_allclose(res.sigma_halko.cpu().numpy()[f], ref.sigma_halko, rtol=tol)
+        assert rs.principal_angle(res.V.cpu().numpy()[f], ref.V) < 1e-5
+        assert rs.principal_angle(res.U.cpu().numpy()[f], ref.U) < 1e-5
+
+
+def test_operator_rejects_bad_closure_masks(env):
+    torch, rr = env
+    import dataclasses
+    g = W.ns_grid(6, 5)
+    for bad in [dataclasses.replace(g, neumann=(8, 0, 0, 0)),
+                dataclasses.replace(g, neumann=(0, 0, 1, 0), periodic_y=True)]:
+        with pytest.raises(rr.RRError) as e:
+            rr.Operator(bad, W.shear_bubble_flow(g))
+        assert e.value.status == 1

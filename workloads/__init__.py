@@ -37,6 +37,10 @@ class Grid:
     sponge_max: float = 0.0
     sponge_frac: float = 0.1
     periodic_y: bool = False
+    # boundary closure: per side (x0, x1, y0, y1) a bit mask over the q
+    # variables whose ghost node equals the adjacent interior node (Neumann);
+    # clear bits keep the zero (Dirichlet) ghost
+    neumann: tuple = (0, 0, 0, 0)
 
     @property
     def q(self) -> int:
@@ -148,9 +152,17 @@ def log_omegas(n: int, lo: float = 0.1, hi: float = 5.0) -> np.ndarray:
     return np.exp(np.linspace(math.log(lo), math.log(hi), n))
 
 
-def ns_grid(nx: int, ny: int, re: float = 500.0, mach: float = 0.3) -> Grid:
+# Sec. III.A's closure in (rho', u', v'): Neumann pressure (= rho' in the
+# isothermal model) with Dirichlet velocities at the far field, Neumann for
+# every variable at the outlet x1
+PAPER_NEUMANN = (1, 7, 1, 1)
+
+
+def ns_grid(nx: int, ny: int, re: float = 500.0, mach: float = 0.3,
+            neumann: tuple = (0, 0, 0, 0)) -> Grid:
     return Grid(kind=KIND_NS2D, nx=nx, ny=ny, x0=0.0, x1=20.0, y0=-5.0,
-                y1=5.0, re=re, mach=mach, sponge_max=1.0, sponge_frac=0.1)
+                y1=5.0, re=re, mach=mach, sponge_max=1.0, sponge_frac=0.1,
+                neumann=tuple(neumann))
 
 
 def config_tiny() -> Workload:
