@@ -297,6 +297,39 @@ __global__ void right_mul_kernel(int N, int k, int RB, const double2* Y,
   }
 }
 
+// out = Y S with S upper triangular (S[m][j] = 0 for m > j, as the inverse
+// Cholesky factors are): column j sums m <= j only, in the same order as the
+// dense kernel.  A thread takes the column pair (j, k-1-j), so every thread
+// runs k+1 multiply-adds and the FP64 work halves.
+__global__ void right_mul_upper_kernel(int N, int k, int RB, const double2* Y,
+                                       const double2* __restrict__ Sall, double2* out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* S = reinterpret_cast<double2*>(smem_raw);  // [k][k]
+  double2* Yr = S + k * k;                             // [RB][k]
+  const int f = blockIdx.y;
+  const int kk = k * k, kh = (k + 1) / 2;
+  for (int e = threadIdx.x; e < kk; e += blockDim.x) S[e] = Sall[(size_t)f * kk + e];
+  const double2* Yf = Y + (size_t)f * N * k;
+  double2* of = out + (size_t)f * N * k;
+  for (int n0 = blockIdx.x * RB; n0 < N; n0 += gridDim.x * RB) {
+    const int rows = min(RB, N - n0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * k; e += blockDim.x) Yr[e] = Yf[(size_t)n0 * k + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * kh; e += blockDim.x) {
+      const int r = e / kh, j1 = e - r * kh, j2 = k - 1 - j1;
+      const double2* yr = Yr + r * k;
+      double2 s1 = make_double2(0.0, 0.0), s2 = make_double2(0.0, 0.0);
+      for (int m = 0; m <= j1; ++m) s1 = cfma(yr[m], S[m * k + j1], s1);
+      of[(size_t)(n0 + r) * k + j1] = s1;
+      if (j2 != j1) {
+        for (int m = 0; m <= j2; ++m) s2 = cfma(yr[m], S[m * k + j2], s2);
+        of[(size_t)(n0 + r) * k + j2] = s2;
+      }
+    }
+  }
+}
+
 __global__ void small_mul_kernel(int k, const double2* __restrict__ A, const double2* __restrict__ B,
                                  double2* __restrict__ C) {
   const int f = blockIdx.x, kk = k * k;
@@ -584,19 +617,24 @@ rr_status launch_cholesky(int F, int k, const double2* G, double2* R, double2* R
 }
 
 rr_status launch_right_mul(int F, int N, int k, const double2* Y, const double2* S, double2* out,
-                           cudaStream_t st) {
+                           cudaStream_t st, int upper) {
   int RB = 64;
   size_t smem = ((size_t)k * k + (size_t)RB * k) * sizeof(double2);
   static bool attr = false;
   if (!attr) {
     RR_CUDA(cudaFuncSetAttribute(right_mul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  160 * 1024));
+    RR_CUDA(cudaFuncSetAttribute(right_mul_upper_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
     attr = true;
   }
   int nb = (N + RB - 1) / RB;
   if (nb > 152 * 4 / (F > 0 ? F : 1) + 1) nb = 152 * 4 / (F > 0 ? F : 1) + 1;
   prof_begin(PROF_RIGHTMUL, st);
-  right_mul_kernel<<<dim3(nb, F), 256, smem, st>>>(N, k, RB, Y, S, out);
+  if (upper)
+    right_mul_upper_kernel<<<dim3(nb, F), 256, smem, st>>>(N, k, RB, Y, S, out);
+  else
+    right_mul_kernel<<<dim3(nb, F), 256, smem, st>>>(N, k, RB, Y, S, out);
   prof_end(PROF_RIGHTMUL, st);
   RR_CUDA(cudaGetLastError());
   return RR_OK;

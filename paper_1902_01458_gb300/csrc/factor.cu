@@ -233,45 +233,28 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
     if (lane == 0) s_nk = cnt;
   }
 
-  // inverses of U11 (warp 0) and of the unit lower L11 (warp 1), rows =
-  // chosen slots in order, one column per lane held in registers; then
+  // inverses of U11 (warp 0) and of the unit lower L11 (warp 1) in parallel,
+  // rows = chosen slots in order, one column per lane; then
   // T^{-1} = U11^{-1} L11^{-1}
   if (warp == 0 && lane < nbk) {
     const int c = lane;
-    C u[NB];
-#pragma unroll
-    for (int i = NB - 1; i >= 0; --i) {
-      u[i] = czero<C>();
-      if (i <= c) {
-        const C* row = P + chosen[i] * PS;
-        C sacc = (i == c) ? mk((T)1, (T)0) : czero<C>();
-#pragma unroll
-        for (int m = i + 1; m < NB; ++m)
-          if (m <= c) sacc = csub(sacc, cmul(row[m], u[m]));
-        u[i] = cmul(sacc, cinv(row[i]));
-      }
+    for (int i = 0; i < NB; ++i) Ui[i][c] = czero<C>();
+    for (int i = c; i >= 0; --i) {
+      const C* row = P + chosen[i] * PS;
+      C sacc = (i == c) ? mk((T)1, (T)0) : czero<C>();
+      for (int m = i + 1; m <= c; ++m) sacc = csub(sacc, cmul(row[m], Ui[m][c]));
+      Ui[i][c] = cmul(sacc, cinv(row[i]));
     }
-#pragma unroll
-    for (int i = 0; i < NB; ++i) Ui[i][c] = u[i];
   } else if (warp == 1 && lane < nbk) {
     const int c = lane;
-    C l[NB];
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      l[i] = czero<C>();
-      if (i == c) {
-        l[i] = mk((T)1, (T)0);
-      } else if (i > c && i < nbk) {
-        const C* row = P + chosen[i] * PS;
-        C sacc = czero<C>();
-#pragma unroll
-        for (int m = 0; m < i; ++m)
-          if (m >= c) sacc = csub(sacc, cmul(row[m], l[m]));
-        l[i] = sacc;
-      }
+    for (int i = 0; i < NB; ++i) Li[i][c] = czero<C>();
+    Li[c][c] = mk((T)1, (T)0);
+    for (int i = c + 1; i < nbk; ++i) {
+      const C* row = P + chosen[i] * PS;
+      C sacc = czero<C>();
+      for (int m = c; m < i; ++m) sacc = csub(sacc, cmul(row[m], Li[m][c]));
+      Li[i][c] = sacc;
     }
-#pragma unroll
-    for (int i = 0; i < NB; ++i) Li[i][c] = l[i];
   }
   __syncthreads();
   for (int e = tid; e < nbk * nbk; e += nt) {

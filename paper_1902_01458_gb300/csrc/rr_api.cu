@@ -343,7 +343,7 @@ rr_status cholqr2(rr_factors* fa, int k, double2* Y, double2* Rout, Work& w, rr_
   }
   for (int f = 0; f < F; ++f)
     if (info) info->cqr_cond = std::max(info->cqr_cond, cond[f]);
-  if ((s = launch_right_mul(F, N, k, Y, w.R1i, Y, st)) != RR_OK) return s;
+  if ((s = launch_right_mul(F, N, k, Y, w.R1i, Y, st, 1)) != RR_OK) return s;
   RR_CUDA(cudaMemcpyAsync(w.Rt, w.R1, (size_t)F * k * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   for (int p = 1; p < passes; ++p) {
     RR_CUDA(cudaMemsetAsync(w.bad, 0, F * sizeof(int), st));
@@ -352,7 +352,7 @@ rr_status cholqr2(rr_factors* fa, int k, double2* Y, double2* Rout, Work& w, rr_
     if (defer_rinv && p + 1 == passes)
       RR_CUDA(cudaMemcpyAsync(defer_rinv, w.R2i, (size_t)F * k * k * sizeof(double2),
                               cudaMemcpyDeviceToDevice, st));
-    else if ((s = launch_right_mul(F, N, k, Y, w.R2i, Y, st)) != RR_OK)
+    else if ((s = launch_right_mul(F, N, k, Y, w.R2i, Y, st, 1)) != RR_OK)
       return s;
     if ((s = launch_small_mul(F, k, w.R2, w.Rt, w.R1, st)) != RR_OK) return s;
     RR_CUDA(cudaMemcpyAsync(w.Rt, w.R1, (size_t)F * k * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));

@@ -220,8 +220,9 @@ rr_status launch_gram(int F, int N, int k, const double2* Y, double2* part, int 
                       double2* G, cudaStream_t st);
 rr_status launch_cholesky(int F, int k, const double2* G, double2* R, double2* Rinv,
                           int* bad, double shift_rel, double* cond, cudaStream_t st);
+// upper != 0: S is upper triangular (the kernel skips its zero lower part)
 rr_status launch_right_mul(int F, int N, int k, const double2* Y, const double2* S,
-                           double2* out, cudaStream_t st);
+                           double2* out, cudaStream_t st, int upper = 0);
 rr_status launch_small_mul(int F, int k, const double2* A, const double2* B, double2* C,
                            cudaStream_t st);
 rr_status launch_jacobi_svd(int F, int k, const double2* R, double* sigma, double2* Ul,
