@@ -35,11 +35,14 @@ import workloads as W  # noqa: E402
 
 HBM_PEAK_GBS = 6800.0       # profiling-recipe fallback (no MEASURED_PEAKS.json)
 BF16_PEAK_TFLOPS = 1900.0   # fallback burst figure
-# DRAM bytes (read + write) per launch of the timed kernel class, averaged over
-# its launches, from the ncu captures summarised in profiles/; None until the
-# current kernels have been captured
-UPDATE_TRAFFIC = None
-SWEEP_TRAFFIC = None
+# DRAM bytes (read + write) per launch of the timed kernel class from the ncu
+# captures summarised in profiles/ (batch 64, block 768; per-launch traffic
+# does not depend on nx).  Update: next-panel slice 25.2 MB (its writes stay
+# in L2), rest of the matrix 510.6 MB, averaged over the 11,776 + 12,288
+# launches of one factorisation.  Sweep: sweep_tc2_kernel, 315.0 MB read +
+# 26 MB written per column step.
+UPDATE_TRAFFIC = (11776 * 25.2e6 + 12288 * 510.6e6) / 24064
+SWEEP_TRAFFIC = 341.0e6
 
 
 def parse():
