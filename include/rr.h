@@ -49,7 +49,7 @@ typedef enum {
   RR_ERR_RANK = 5,        /* CholeskyQR breakdown even with the shift        */
   RR_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up              */
   RR_ERR_CUDA = 7,        /* CUDA runtime error (message in rr_last_error)   */
-  RR_ERR_UNSUPPORTED = 8  /* valid request this build does not implement     */
+  RR_ERR_UNSUPPORTED = 8  /* valid request the library does not implement   */
 } rr_status;
 
 /* Arithmetic of the block factorisation and the block sweeps.  FP64 runs
@@ -194,7 +194,7 @@ rr_status rr_sketch(rr_factors* f, int k, const uint64_t* seeds,
                     const double* phi, double refine_tol, int max_refine,
                     void* V, double* sigma_halko, rr_info* info);
 
-/* Test matrices of Sec. II.C, all drawn from one Philox-4x32-10 block per
+/* Test matrices of Sec. II.B.2, all drawn from one Philox-4x32-10 block per
  * entry (key seeds[f], counter (n, j, 0, 0); words w0..w3):
  *  RR_OMEGA_GAUSSIAN          Box-Muller N(0, 1) as described at rr_sketch;
  *  RR_OMEGA_RADEMACHER        -1 if bit 0 of w0 is set, else +1;
@@ -214,7 +214,7 @@ typedef enum {
 } rr_omega_kind;
 
 /* Options of rr_sketch_ex.  power_iters = q runs q subspace iterations
- * (Sec. II.C; Halko, Martinsson & Tropp 2011, Alg. 4.4) after the sketch:
+ * (Sec. II.B.1; Halko, Martinsson & Tropp 2011, Alg. 4.4) after the sketch:
  * q times { Z = qr(R^H Q); Q = qr(R Z) }, every QR a CholeskyQR2, every
  * solve reusing the factors (2k extra solves per iteration).  density is
  * read only for RR_OMEGA_SPARSE_RADEMACHER. */
@@ -290,7 +290,7 @@ rr_status rr_refactor(rr_factors* f, const double* shifts);
 
 /* ------------------------------------------------------------ batch plans
  * Many resolvent problems of uneven size (grids, shifts, k) as one CUDA
- * graph.  The paper sweeps the frequency (Sec. IV) with one factorisation
+ * graph.  The paper sweeps the frequency (Sec. III.B) with one factorisation
  * per frequency (Sec. III.A); the frequencies are independent problems, so a
  * plan runs them together:
  *  - problems that share an operator form a group with ONE batched block
@@ -307,8 +307,8 @@ rr_status rr_refactor(rr_factors* f, const double* shifts);
  *    candidates: the trailing-update kernel of each group's factorisation
  *    (128 x 64 tensor-core tiles or 64 x 64 CUDA-core tiles, on its first
  *    columns), the K-split (1..4 or the built-in choice) of each
- *    sub-batch's tensor-core sweep, and the number of lanes (1, 2, 4, 8,
- *    all groups; whole-graph runs).
+ *    sub-batch's tensor-core sweep, and the number of lanes (2, 4, 8, all
+ *    groups, and 1 for plans of at most two groups; whole-graph runs).
  * A run reproduces the calibration run's arithmetic (same kernels, same
  * order); after it, the factor flags and a device log of every solve's
  * final residual and every QR's breakdown flag are checked on the host.

@@ -1,5 +1,5 @@
 """Oracle: discrete linearised operator L (Sec. II.A, Eq. 1) and sketch
-weight Phi (Sec. III.C, Eq. 9).  Test infrastructure only.
+weight Phi (Sec. III.D, Eq. 9).  Test infrastructure only.
 
 The paper gives no discrete equations for its operator.  The operators here
 follow the reading fixed for this project:

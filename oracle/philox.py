@@ -1,4 +1,4 @@
-"""Oracle: Gaussian test matrix Omega (Algorithm 1, first step; Sec. II.C).
+"""Oracle: Gaussian test matrix Omega (Algorithm 1, first step; Sec. II.B.2).
 
 Test infrastructure only.  Entries come from the counter-based generator
 Philox-4x32-10 of Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as
@@ -16,7 +16,7 @@ Box-Muller transform in FP64:
 Omega itself is real N(0, 1) (stored complex with zero imaginary part), or
 diag(Phi) times it for the physics-informed test matrix of Eq. (9).
 
-The other test matrices Sec. II.C names take their entries from the same
+The other test matrices Sec. II.B.2 names take their entries from the same
 Philox words (counter (n, j, 0, 0)):
 
 * Rademacher (Clarkson & Woodruff 2009): +1 if bit 0 of w0 is 0, else -1;
@@ -109,7 +109,7 @@ def test_matrix(seed: int, n_rows: int, k: int, phi=None, kind: str = "gaussian"
     """Omega (complex128, [N, k]); with phi (length N) Omega_p = diag(phi) Omega.
 
     kind "orthonormal" returns diag(phi) G before its QR; resolvent.py takes
-    the QR (the orthonormalised test matrix of Sec. II.C)."""
+    the QR (the orthonormalised test matrix of Sec. II.B.2)."""
     if kind in ("gaussian", "orthonormal"):
         g = gaussian(seed, n_rows, k)
     elif kind == "rademacher":

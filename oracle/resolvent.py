@@ -152,9 +152,9 @@ def randomized(L: sp.spmatrix, s: complex, k: int, seed: int, phi=None,
       sigma_j <- ||(U Sigma)_j||,  u_j <- (U Sigma)_j / sigma_j
       optionally (U, Sigma, Vt) <- svd(U Sigma), V <- V Vt
 
-    kind selects the test matrix of Sec. II.C (see philox.py); "orthonormal"
+    kind selects the test matrix of Sec. II.B.2 (see philox.py); "orthonormal"
     replaces Omega by the Q factor of diag(Phi) G.  power_iters = q > 0 runs
-    q subspace iterations (Sec. II.C; Halko, Martinsson & Tropp 2011,
+    q subspace iterations (Sec. II.B.1; Halko, Martinsson & Tropp 2011,
     Alg. 4.4) after the sketch, a QR between every two applications:
       for each of q passes:  Z <- qr(R^H Q);  Q <- qr(R Z)
     """

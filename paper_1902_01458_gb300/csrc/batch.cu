@@ -1,5 +1,5 @@
 // Batch plans: many resolvent problems of uneven size (grids, k, shifts) as
-// one CUDA graph.  Frequencies are independent problems (Sec. IV sweeps the
+// one CUDA graph.  Frequencies are independent problems (Sec. III.B sweeps the
 // frequency; Sec. III.A factors once per frequency), so a plan
 //   - groups the problems by operator: one batched block factorisation per
 //     group over its shifts (the kernels of factor.cu take F problems),
@@ -522,8 +522,11 @@ extern "C" rr_status rr_batch_create(int nprob, const rr_problem* probs, rr_prec
   if (o.lanes > 0) {
     cands.push_back(std::min(o.lanes, ngroups));
   } else if (o.tune) {
+    // one lane (fully serial groups) is timed only for tiny plans
     for (int L : {1, 2, 4, 8, ngroups})
-      if (L <= ngroups && std::find(cands.begin(), cands.end(), L) == cands.end()) cands.push_back(L);
+      if (L <= ngroups && (L > 1 || ngroups <= 2) &&
+          std::find(cands.begin(), cands.end(), L) == cands.end())
+        cands.push_back(L);
   } else {
     cands.push_back(std::min(ngroups, 4));
   }

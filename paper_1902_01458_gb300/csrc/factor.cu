@@ -214,16 +214,18 @@ gj_panel_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall, int* __restri
       if (lane == j) kc = cq;
       if (inK && lane == ql) kc = ca;
       if (!inK && lane == ql) nc = ca;
-      if (lane == 0) {
-        ipiv[j] = q;
-        if (q != k0 + j) {
-          int t = perm[k0 + j];
-          perm[k0 + j] = perm[q];
-          perm[q] = t;
-        }
-      }
+      if (lane == 0) ipiv[j] = q;
       __syncwarp();
     }
+    // perm undergoes the same interchanges: every position that received
+    // another slot takes that slot's old entry (all reads before any write,
+    // instead of a chain of dependent global swaps)
+    const bool movedK = lane < nbk && kc != k0 + lane;
+    const int pk = movedK ? perm[kc] : 0;
+    const int pn = lane < cnt ? perm[nc] : 0;
+    __syncwarp();
+    if (movedK) perm[k0 + lane] = pk;
+    if (lane < cnt) perm[np] = pn;
     if (lane < nbk) sigK[lane] = kc;
     if (lane < cnt) {
       nkPos[lane] = np;
@@ -337,11 +339,14 @@ gj_rowblock_kernel(int b, int k0, int nbk, C_t<T>* __restrict__ Mall,
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     for (int j = lane; j < NB; j += 32) srcK[j] = k0 + j;
+    // the panel's interchanges, one per lane, read once (not one dependent
+    // global load per step of the serial loop below)
+    const int piv_l = lane < nbk ? ipiv_all[f * 32 + lane] : 0;
     int myPos = -1, myCont = -1, nk = 0;
     __syncwarp();
     for (int j = 0; j < nbk; ++j) {
       const int a = k0 + j;
-      const int p = ipiv_all[f * 32 + j];
+      const int p = __shfl_sync(0xffffffffu, piv_l, j);
       if (p == a) continue;
       if (p < k0 + nbk) {
         if (lane == 0) {

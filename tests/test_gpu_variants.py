@@ -1,5 +1,5 @@
-"""GPU parity of the test-matrix variants and of subspace iterations
-(Sec. II.C) through the C ABI, against the oracle on the same seeds.
+"""GPU parity of the test-matrix variants (Sec. II.B.2) and of subspace
+iterations (Sec. II.B.1) through the C ABI, against the oracle on the same seeds.
 
 Rademacher and sparse Rademacher entries are integer decisions on Philox
 words followed by one multiply by Phi: bit-exact.  Sketch results carry the

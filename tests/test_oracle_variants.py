@@ -1,6 +1,6 @@
 """Pins of the oracle's test-matrix variants (Rademacher, sparse Rademacher,
-orthonormalised Gaussian; Sec. II.C) and of its subspace (power) iterations
-(Sec. II.C), against what probability and linear algebra fix: exact value
+orthonormalised Gaussian; Sec. II.B.2) and of its subspace (power) iterations
+(Sec. II.B.1), against what probability and linear algebra fix: exact value
 sets, binomial counts, range identities, the dense matrix-power definition of
 the iteration and the Halko-Martinsson-Tropp bound with power iterations."""
 import math

@@ -1,5 +1,5 @@
-"""Frequency sharding across ranks: independent problems, no
-data-path collective.  Two gloo ranks on CPU check that the bench's batch
+"""Frequency sharding across ranks: independent problems (Sec. III.B sweeps the
+frequency), no data-path collective.  Two gloo ranks on CPU check that the bench's batch
 assignment covers every frequency exactly once per round of steps, with the
 seed convention 1000 + frequency index, and that the max-over-ranks timing
 reduction works."""
