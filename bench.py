@@ -200,6 +200,19 @@ def panel_width(prec_bytes, b):
     return 8
 
 
+def metric_name(g, k):
+    """The headline metric, shared by both arms so their lines compare."""
+    return f"resolvent frequencies/sec at N={g.n:,}, k={k}"
+
+
+def workload_config(g, k, world):
+    """The workload both arms run (the implementations differ, the work does not)."""
+    return {"workload": f"ns2d-{g.nx}x{g.ny}-k{k}", "N": g.n, "block": g.b, "k": k,
+            "omega": "64 log-spaced in [0.1, 5]", "phi_weighted": True,
+            "l2": "inputs larger than L2 (factors 4.8 GB per frequency at 512x256)",
+            "parallelism": f"frequency shards x{world}"}
+
+
 # ---------------------------------------------------------------- CPU oracle
 def cpu_oracle_sample(grid_full, k, nx_sample, omega, seed):
     """Time the FP64 oracle (banded LAPACK LU, Householder QR, LAPACK SVD) on
@@ -237,12 +250,12 @@ def run_reference(args):
     value = 1.0 / per_freq
     cores = os.cpu_count()
     line = {
-        "impl": "reference", "metric": "resolvent frequencies/sec at N=393,216, k=32",
+        "impl": "reference", "metric": metric_name(g, args.k),
         "value": value, "unit": "frequencies/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_freq * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"ns2d-{g.nx}x{g.ny}-k{args.k}", "N": g.n, "k": args.k,
-                   "block": g.b, "precision": "fp64 CPU oracle"},
+        "config": workload_config(g, args.k, world),
+        "precision": "fp64 CPU oracle (banded LAPACK LU, Householder QR, LAPACK SVD)",
         "cpu_baseline": {"value": value, "unit": "frequencies/s", "cores": cores,
                          "kind": "oracle",
                          "sample": f"one frequency per step on the first {nx_s} of {g.nx} "
@@ -431,17 +444,14 @@ def run_ours(args):
 
     if rank == 0:
         line = {
-            "metric": f"resolvent frequencies/sec at N={g.n:,}, k={k} (mixed FP32+FP64 refinement)",
+            "metric": metric_name(g, k),
             "value": value, "unit": "frequencies/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64+f64", "data": "synthetic",
-            "config": {"workload": f"ns2d-{g.nx}x{g.ny}-k{k}", "N": g.n, "block": g.b,
-                       "k": k, "frequencies_per_step_per_gpu": F, "omega": "log [0.1,5], 64",
-                       "precision": "fp32 factors/sweeps, fp64 refinement to 1e-10, "
-                                    "fp64 CholeskyQR2 + Jacobi SVD",
-                       "l2": "inputs larger than L2 (factors 4.8 GB per frequency)",
-                       "parallelism": f"frequency shards x{world}"},
+            "config": workload_config(g, k, world), "frequencies_per_step_per_gpu": F,
+            "precision": "mixed: fp32 factors and tensor-core sweeps, fp64 refinement to "
+                         "1e-10, fp64 CholeskyQR2 + Jacobi SVD",
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
             "clocks": clocks, "gpu_launches": launches,
             "refine": {"iters": max(info_last[0]["refine_iters"], info_last[1]["refine_iters"]),
