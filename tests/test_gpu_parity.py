@@ -309,3 +309,26 @@ def test_operator_rejects_bad_closure_masks(env):
         with pytest.raises(rr.RRError) as e:
             rr.Operator(bad, W.shear_bubble_flow(g))
         assert e.value.status == 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_solve_at_the_largest_block(env, precision, adjoint):
+    """b = 1020, next to the 1024 maximum: the narrowest panels (16 columns in
+    FP32, 8 in FP64, set by shared memory) and the largest sweep tiles."""
+    torch, rr = env
+    g = W.ns_grid(4, 340)
+    flow = W.smooth_random_flow(g, 5)
+    L = op.assemble(g, flow)
+    o = rr.Operator(g, flow)
+    shifts = np.array([0.4j, 2.1j])
+    fa = o.factor(shifts, precision)
+    rng = np.random.default_rng(13)
+    k = 4
+    b = rng.standard_normal((2, g.n, k)) + 1j * rng.standard_normal((2, g.n, k))
+    x, info = fa.solve(to_dev(b, torch), adjoint=adjoint, refine_tol=1e-12, max_refine=20)
+    x = x.cpu().numpy()
+    for f, s in enumerate(shifts):
+        A = op.shifted(L, s).toarray()
+        want = np.linalg.solve(A.conj().T if adjoint else A, b[f])
+        assert rel_err(x[f], want) < (1e-11 if precision == "fp64" else 1e-9), f
