@@ -157,3 +157,15 @@ def test_batched_workload_full_size_sampled(env):
         nrm = torch.linalg.vector_norm(o["U"], dim=0).cpu().numpy()
         np.testing.assert_allclose(nrm, 1.0, rtol=1e-12)
     b.close()
+
+
+def test_single_problem_batch_matches_oracle(env):
+    """The smallest plan: one problem, one group, one sub-batch, one lane."""
+    torch, rr = env
+    ops, problems = _build(rr, [(5, 48, 6, 1.7)])
+    b = rr.Batch(problems, precision="fp32", tune=True)
+    b.run()
+    d = b.describe()
+    assert d["groups"] == 1 and d["views"] == 1 and d["lanes"] == 1
+    _check_against_oracle(ops, problems, b.outputs, [problems[0]["shift"]], 1e-6)
+    b.close()
