@@ -10,9 +10,14 @@ QR is Householder (the CUDA path uses CholeskyQR2) and the small SVD is
 LAPACK's (the CUDA path uses one-sided Jacobi).
 
 Modules
-  operator   -- the linearised operator L and the sketch weight Phi
-  philox     -- Philox-4x32-10 counter-based generator and Gaussian entries
-  resolvent  -- exact resolvent SVD and Algorithm 1 step by step
+  operator   -- the linearised operator L (Dirichlet or Neumann closure) and
+                the sketch weight Phi
+  philox     -- Philox-4x32-10 counter-based generator and the test-matrix
+                entries (Gaussian, Rademacher, sparse Rademacher)
+  resolvent  -- exact resolvent SVD, Algorithm 1 step by step, subspace
+                iterations
+  gradient   -- gradient of the summed leading gains with respect to the base
+                flow
 
 Functions whose results are pinned only against the paper's statements and
 not against closed forms are marked "parity unpinned" in their docstrings.
