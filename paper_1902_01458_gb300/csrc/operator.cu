@@ -183,17 +183,19 @@ __global__ void assemble_kernel(AsmParams p, const double* __restrict__ flow,
   }
 }
 
-// y = (s I - L) x (adjoint: (s I - L)^H x), optionally r = b - that.
-// Block (blockIdx.y = problem f) of rows x columns: a group of tpr threads
-// shares one row n and covers its k columns (coalesced [n][k] accesses, the
-// row's stencil read once per group through L1); all index arithmetic is
-// 32-bit and done once per row; Q (unknowns per point) is a template
-// parameter so the 9 x Q stencil loop unrolls and its loads issue together.
+// y = (s I - L)^H x, optionally r = b - that (the forward product uses the
+// ELL kernel below).  Block (blockIdx.y = problem f) of rows x columns: a
+// group of tpr threads shares one row n and covers its k columns (coalesced
+// [n][k] accesses, the stencil entries read once per group through L1); all
+// index arithmetic is 32-bit and done once per row; Q (unknowns per point) is
+// a template parameter so the 9 x Q stencil loop unrolls and its loads issue
+// together.  (L^T x)[n] sums over the rows r whose stencil reaches n: row r
+// at point (ix - dx, iy - dy) reaches n through its slot (dx, dy).
 template <bool RESID, int Q>
 __global__ void __launch_bounds__(256)
-apply_kernel(OpView op, const double2* __restrict__ shifts, int k, int adjoint,
-             const double2* __restrict__ bvec, const double2* __restrict__ x,
-             double2* __restrict__ y) {
+apply_adjoint_kernel(OpView op, const double2* __restrict__ shifts, int k,
+                     const double2* __restrict__ bvec, const double2* __restrict__ x,
+                     double2* __restrict__ y) {
   const int f = blockIdx.y;
   const int tpr = k < (int)blockDim.x ? k : (int)blockDim.x;
   const int rows_per = blockDim.x / tpr;
@@ -203,48 +205,32 @@ apply_kernel(OpView op, const double2* __restrict__ shifts, int k, int adjoint,
   const double2* xf = x + (size_t)f * NK;
   double2* yf = y + (size_t)f * NK;
   const double2* bf = RESID ? bvec + (size_t)f * NK : nullptr;
-  double2 s = shifts[f];
-  if (adjoint) s.y = -s.y;
+  const double2 s = make_double2(shifts[f].x, -shifts[f].y);
   constexpr int q = Q, S = 9 * Q;
   for (int n = blockIdx.x * rows_per + rsub; n < op.n; n += gridDim.x * rows_per) {
     const int pt = n / q, c = n - pt * q;
     const int ix = pt / op.ny, iy = pt - ix * op.ny;
-    // neighbour point bases (-1: Dirichlet ghost), slot (dx+1)*3 + (dy+1)
+    // bases of the points whose stencils reach n (-1: Dirichlet ghost)
     int nb[9];
 #pragma unroll
     for (int dx = -1; dx <= 1; ++dx)
 #pragma unroll
       for (int dy = -1; dy <= 1; ++dy) {
-        const int jx = adjoint ? ix - dx : ix + dx;
-        const int jy = nbr_y(iy, adjoint ? -dy : dy, op.ny, op.periodic);
+        const int jx = ix - dx;
+        const int jy = nbr_y(iy, -dy, op.ny, op.periodic);
         nb[(dx + 1) * 3 + (dy + 1)] =
             (jx >= 0 && jx < op.nx && jy >= 0) ? (jx * op.ny + jy) * q : -1;
       }
-    const double* cf = op.coef + (size_t)n * S;
     for (int j = jt; j < k; j += tpr) {
       double2 acc = cmul(s, xf[(size_t)n * k + j]);
-      if (!adjoint) {
 #pragma unroll
-        for (int sl = 0; sl < 9; ++sl) {
-          const int base = nb[sl];
-          if (base < 0) continue;
-          const double* cs = cf + sl * q;
+      for (int sl = 0; sl < 9; ++sl) {
+        const int base = nb[sl];
+        if (base < 0) continue;
 #pragma unroll
-          for (int cp = 0; cp < q; ++cp)
-            acc = crfma(-cs[cp], xf[(size_t)(base + cp) * k + j], acc);
-        }
-      } else {
-        // (L^T x)[n] = sum over rows r whose stencil reaches n: row r at
-        // point (ix - dx, iy - dy) reaches n through its slot (dx, dy)
-#pragma unroll
-        for (int sl = 0; sl < 9; ++sl) {
-          const int base = nb[sl];
-          if (base < 0) continue;
-#pragma unroll
-          for (int cr = 0; cr < q; ++cr) {
-            const double a = op.coef[(size_t)(base + cr) * S + sl * q + c];
-            acc = crfma(-a, xf[(size_t)(base + cr) * k + j], acc);
-          }
+        for (int cr = 0; cr < q; ++cr) {
+          const double a = op.coef[(size_t)(base + cr) * S + sl * q + c];
+          acc = crfma(-a, xf[(size_t)(base + cr) * k + j], acc);
         }
       }
       if (RESID) {
@@ -253,6 +239,92 @@ apply_kernel(OpView op, const double2* __restrict__ shifts, int k, int adjoint,
       }
       yf[(size_t)n * k + j] = acc;
     }
+  }
+}
+
+// y = (s I - L) x (or r = b - that) from the ELL copy of the stencil: a
+// row's nonzero entries in slot order, the same sum as over all 9q slots
+// (the skipped terms are zero).  The width WT is a compile-time constant so
+// the loop runs exactly WT multiply-adds per entry: the kernel is bound by
+// the FP64 pipe, and the Navier-Stokes rows have at most 13 of their 27
+// slots nonzero.  Threads as in apply_adjoint_kernel.
+template <bool RESID, int WT>
+__global__ void __launch_bounds__(256)
+apply_ell_kernel(OpView op, const double2* __restrict__ shifts, int k,
+                 const double2* __restrict__ bvec, const double2* __restrict__ x,
+                 double2* __restrict__ y) {
+  const int f = blockIdx.y;
+  const int tpr = k < (int)blockDim.x ? k : (int)blockDim.x;
+  const int rows_per = blockDim.x / tpr;
+  const int rsub = threadIdx.x / tpr, jt = threadIdx.x - rsub * tpr;
+  if (rsub >= rows_per) return;
+  const size_t NK = (size_t)op.n * k;
+  const double2* xf = x + (size_t)f * NK;
+  double2* yf = y + (size_t)f * NK;
+  const double2* bf = RESID ? bvec + (size_t)f * NK : nullptr;
+  const double2 s = shifts[f];
+  for (int n = blockIdx.x * rows_per + rsub; n < op.n; n += gridDim.x * rows_per) {
+    const double* ev = op.ell_val + (size_t)n * WT;
+    const int* ec = op.ell_col + (size_t)n * WT;
+    double a[WT];
+    int m[WT];
+#pragma unroll
+    for (int t = 0; t < WT; ++t) {
+      a[t] = ev[t];
+      m[t] = ec[t];
+    }
+    for (int j = jt; j < k; j += tpr) {
+      double2 acc = cmul(s, xf[(size_t)n * k + j]);
+#pragma unroll
+      for (int t = 0; t < WT; ++t) acc = crfma(-a[t], xf[(size_t)m[t] * k + j], acc);
+      if (RESID) {
+        const double2 bb = bf[(size_t)n * k + j];
+        acc = mk(bb.x - acc.x, bb.y - acc.y);
+      }
+      yf[(size_t)n * k + j] = acc;
+    }
+  }
+}
+
+// Widths the ELL apply kernel is compiled for; a row set is padded to the
+// smallest one that holds its widest row.
+constexpr int kEllWidths[] = {4, 6, 8, 10, 13, 16, 20, 27};
+
+// ELL copy of the stencil: the widest row, then every row's nonzero entries
+// in slot order, padded with zero entries on the row itself.
+__global__ void ell_count_kernel(OpView op, int* wmax) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= op.n) return;
+  const double* cf = op.coef + (size_t)n * op.S;
+  int cnt = 0;
+  for (int e = 0; e < op.S; ++e) cnt += cf[e] != 0.0 ? 1 : 0;
+  atomicMax(wmax, cnt);
+}
+
+__global__ void ell_fill_kernel(OpView op, int W, double* __restrict__ val, int* __restrict__ col) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= op.n) return;
+  const int q = op.q, pt = n / q;
+  const int ix = pt / op.ny, iy = pt - ix * op.ny;
+  const double* cf = op.coef + (size_t)n * op.S;
+  double* v = val + (size_t)n * W;
+  int* c = col + (size_t)n * W;
+  int t = 0;
+  for (int sl = 0; sl < 9; ++sl) {
+    const int jx = ix + sl / 3 - 1;
+    const int jy = nbr_y(iy, sl % 3 - 1, op.ny, op.periodic);
+    if (jx < 0 || jx >= op.nx || jy < 0) continue;
+    for (int cp = 0; cp < q; ++cp) {
+      const double a = cf[sl * q + cp];
+      if (a == 0.0 || t >= W) continue;
+      v[t] = a;
+      c[t] = (jx * op.ny + jy) * q + cp;
+      ++t;
+    }
+  }
+  for (; t < W; ++t) {
+    v[t] = 0.0;
+    c[t] = n;
   }
 }
 
@@ -274,6 +346,57 @@ __global__ void round_coef_kernel(const double* __restrict__ in, float* __restri
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x)
     out[e] = (float)in[e];
+}
+
+static dim3 apply_grid(const OpDev& d, int F, int k);
+
+rr_status build_ell(OpDev& d) {
+  int* wdev = nullptr;
+  RR_CUDA(cudaMalloc(&wdev, sizeof(int)));
+  const int blocks = (d.n + 255) / 256;
+  int W = 0;
+  cudaError_t e = cudaMemset(wdev, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    prof_count(1);
+    ell_count_kernel<<<blocks, 256>>>(view(d), wdev);
+    e = cudaMemcpy(&W, wdev, sizeof(int), cudaMemcpyDeviceToHost);
+  }
+  cudaFree(wdev);
+  if (e != cudaSuccess) return cuda_status(e, "ELL stencil width");
+  d.ell_w = kEllWidths[sizeof(kEllWidths) / sizeof(int) - 1];
+  for (int w : kEllWidths)
+    if (w >= W) {
+      d.ell_w = w;
+      break;
+    }
+  RR_CUDA(cudaMalloc(&d.ell_val, (size_t)d.n * d.ell_w * sizeof(double)));
+  RR_CUDA(cudaMalloc(&d.ell_col, (size_t)d.n * d.ell_w * sizeof(int)));
+  prof_count(1);
+  ell_fill_kernel<<<blocks, 256>>>(view(d), d.ell_w, d.ell_val, d.ell_col);
+  RR_CUDA(cudaGetLastError());
+  RR_CUDA(cudaDeviceSynchronize());
+  return RR_OK;
+}
+
+// Forward operator application (adjoint == 0) on the ELL copy, by width.
+template <bool RESID>
+static rr_status launch_ell(const OpDev& d, int F, const double2* shifts, int k,
+                            const double2* b, const double2* x, double2* y, cudaStream_t st) {
+  const dim3 grid = apply_grid(d, F, k);
+  const OpView v = view(d);
+  switch (d.ell_w) {
+    case 4: apply_ell_kernel<RESID, 4><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
+    case 6: apply_ell_kernel<RESID, 6><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
+    case 8: apply_ell_kernel<RESID, 8><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
+    case 10: apply_ell_kernel<RESID, 10><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
+    case 13: apply_ell_kernel<RESID, 13><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
+    case 16: apply_ell_kernel<RESID, 16><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
+    case 20: apply_ell_kernel<RESID, 20><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
+    case 27: apply_ell_kernel<RESID, 27><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
+    default: set_error("ELL width without a compiled kernel"); return RR_ERR_ARG;
+  }
+  RR_CUDA(cudaGetLastError());
+  return RR_OK;
 }
 
 rr_status launch_assemble(OpDev& d, const rr_grid& g, cudaStream_t st) {
@@ -309,12 +432,13 @@ static dim3 apply_grid(const OpDev& d, int F, int k) {
 rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
                        const double2* x, double2* y, cudaStream_t st) {
   prof_count(1);
+  if (!adjoint) return launch_ell<false>(d, F, shifts, k, nullptr, x, y, st);
   if (d.q == 3)
-    apply_kernel<false, 3><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, adjoint,
-                                                                nullptr, x, y);
+    apply_adjoint_kernel<false, 3><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k,
+                                                                        nullptr, x, y);
   else
-    apply_kernel<false, 1><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, adjoint,
-                                                                nullptr, x, y);
+    apply_adjoint_kernel<false, 1><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k,
+                                                                        nullptr, x, y);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }
@@ -389,12 +513,17 @@ extern "C" rr_status rr_apply_static(rr_operator* op, int nshift, const double* 
 rr_status launch_residual(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
                           const double2* b, const double2* x, double2* r, cudaStream_t st) {
   prof_begin(PROF_RESIDUAL, st);
+  if (!adjoint) {
+    rr_status s = launch_ell<true>(d, F, shifts, k, b, x, r, st);
+    prof_end(PROF_RESIDUAL, st);
+    return s;
+  }
   if (d.q == 3)
-    apply_kernel<true, 3><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, adjoint, b, x,
-                                                               r);
+    apply_adjoint_kernel<true, 3><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, b, x,
+                                                                       r);
   else
-    apply_kernel<true, 1><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, adjoint, b, x,
-                                                               r);
+    apply_adjoint_kernel<true, 1><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, b, x,
+                                                                       r);
   prof_end(PROF_RESIDUAL, st);
   RR_CUDA(cudaGetLastError());
   return RR_OK;

@@ -490,9 +490,11 @@ extern "C" rr_status rr_create_operator(const rr_grid* g, const rr_baseflow* fl,
   d.dy = d.periodic ? (g->y1 - g->y0) / g->ny : (g->y1 - g->y0) / (g->ny + 1);
   d.device = device;
   d.coef = nullptr; d.coef32 = nullptr; d.wsqrt = nullptr; d.wisqrt = nullptr; d.flow = nullptr;
+  d.ell_val = nullptr; d.ell_col = nullptr; d.ell_w = 0;
   rr_status s;
   auto fail = [&](rr_status st) {
     cudaFree(d.coef); cudaFree(d.coef32); cudaFree(d.wsqrt); cudaFree(d.wisqrt); cudaFree(d.flow);
+    cudaFree(d.ell_val); cudaFree(d.ell_col);
     delete op;
     return st;
   };
@@ -523,6 +525,7 @@ extern "C" rr_status rr_create_operator(const rr_grid* g, const rr_baseflow* fl,
   if ((s = launch_assemble(d, *g, 0)) != RR_OK) return fail(s);
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(cuda_status(e, "operator assembly"));
+  if ((s = build_ell(d)) != RR_OK) return fail(s);
   *out = op;
   return RR_OK;
 }
@@ -532,6 +535,8 @@ extern "C" rr_status rr_destroy_operator(rr_operator* op) {
   DeviceGuard guard(op->d.device);
   cudaFree(op->d.coef);
   cudaFree(op->d.coef32);
+  cudaFree(op->d.ell_val);
+  cudaFree(op->d.ell_col);
   cudaFree(op->d.wsqrt);
   cudaFree(op->d.wisqrt);
   cudaFree(op->d.flow);

@@ -74,6 +74,12 @@ struct OpDev {
   int kind, q, nx, ny, b, n, periodic;
   double* coef;      // [N][9q]
   float* coef32;     // [N][9q] the same coefficients rounded once to FP32 (FP32 factors)
+  // the nonzero stencil entries of every row in stencil order, padded with
+  // zero entries on the row itself to a width the FP64 apply kernel is
+  // compiled for (ELL layout)
+  double* ell_val;   // [N][ell_w]
+  int* ell_col;      // [N][ell_w] unknown index of the entry
+  int ell_w;
   double* wsqrt;     // [N] W^{1/2} or nullptr (identity)
   double* wisqrt;    // [N] W^{-1/2} or nullptr
   double* flow;      // [3][nx*ny] rho, U, V
@@ -90,13 +96,18 @@ struct rr_operator {
 struct OpView {
   const double* coef;
   const float* coef32;
-  int q, nx, ny, b, n, periodic, S;
+  const double* ell_val;
+  const int* ell_col;
+  int q, nx, ny, b, n, periodic, S, ell_w;
 };
 
 inline OpView view(const OpDev& d) {
   OpView v;
   v.coef = d.coef;
   v.coef32 = d.coef32;
+  v.ell_val = d.ell_val;
+  v.ell_col = d.ell_col;
+  v.ell_w = d.ell_w;
   v.q = d.q; v.nx = d.nx; v.ny = d.ny; v.b = d.b; v.n = d.n;
   v.periodic = d.periodic; v.S = 9 * d.q;
   return v;
@@ -184,6 +195,8 @@ rr_status cuda_status(cudaError_t e, const char* what);
 // ------------------------------------------------------- kernel launchers
 // operator.cu
 rr_status launch_assemble(OpDev& d, const rr_grid& g, cudaStream_t st);
+// ELL copy of the stencil (allocates ell_val / ell_col; synchronous)
+rr_status build_ell(OpDev& d);
 rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
                        const double2* x, double2* y, cudaStream_t st);
 rr_status launch_residual(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
