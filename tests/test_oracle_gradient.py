@@ -111,3 +111,26 @@ def test_gradient_from_given_triplets_is_phase_invariant():
     b = gr.gain_grad_triplets(g, flow, [s], [(S[:2], U[:, :2] * ph, V[:, :2] * ph)], 2,
                               fields=("rho",))
     np.testing.assert_allclose(b, a, rtol=1e-10, atol=1e-14 * np.abs(a).max())
+
+
+def test_gradient_with_neumann_closure_matches_central_differences():
+    """Sec. III.A's closure (Neumann rho' at the far field, every variable at
+    the outlet): the ghost coefficients fold onto boundary nodes, so the
+    gradient's boundary entries change; central differences of the exact
+    objective pin them."""
+    g, flow = _ns_tiny()
+    g = dataclasses.replace(g, neumann=W.PAPER_NEUMANN)
+    shifts = [0.6j]
+    J = 2
+    grad = gr.gain_grad(g, flow, shifts, J)
+    rng = np.random.default_rng(17)
+    for _ in range(2):
+        d = rng.standard_normal((3, g.nx, g.ny))
+        fd = _fd(g, flow, shifts, J, d, 1e-4)
+        assert abs(float(np.sum(grad * d)) - fd) <= 1e-6 * abs(fd)
+    # an outlet node of each field
+    for fi in range(3):
+        d = np.zeros((3, g.nx, g.ny))
+        d[fi, g.nx - 1, 2] = 1.0
+        fd = _fd(g, flow, shifts, J, d, 1e-4)
+        assert abs(grad[fi, g.nx - 1, 2] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(grad).max())
