@@ -151,10 +151,14 @@ rr_status rr_apply(rr_operator* op, int nshift, const double* shifts, int k,
  * 64 KB, held on every GPU that loads the library until the process exits)
  * instead of a cudaMalloc'd buffer; nshift above the maximum is rejected with
  * RR_ERR_ARG.  The call allocates nothing.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
- * the one array, so calls that overlap on the GPU (other streams or host
- * threads) race on it; the call synchronises its stream before returning. */
+ * up the array's device address (cudaGetSymbolAddress, under a host lock)
+ * with that device current and keeps it for the process; a cudaDeviceReset
+ * of that device invalidates the kept address, so do not call this entry
+ * point after resetting a device.  Every call copies the shifts from host
+ * memory and synchronises its stream before returning, so it must not be
+ * called on a capturing stream: it checks and returns RR_ERR_ARG.  All calls
+ * share the one array, so calls that overlap on the GPU (other streams or
+ * host threads) race on it. */
 #define RR_APPLY_STATIC_MAX_SHIFTS 4096
 rr_status rr_apply_static(rr_operator* op, int nshift, const double* shifts, int k,
                           int adjoint, const void* x, void* y, void* stream);
@@ -392,6 +396,17 @@ rr_status rr_batch_destroy(rr_batch* b);
 long long rr_launch_count(void);
 rr_status rr_profile_start(unsigned mask);
 rr_status rr_profile_read(int cls, double* ms, long long* launches);
+
+/* Diagnostics of the bounded device-side waits (no counterpart in the paper;
+ * for tests of the RR_ERR_TIMEOUT path).  Every mbarrier wait of the
+ * tensor-core kernels polls at most `tries` times (0 restores the default,
+ * 2^22) before the kernel records a timeout, drains what it has in flight,
+ * frees its tensor memory and returns; the call that launched it then
+ * returns RR_ERR_TIMEOUT.  stall_launches > 0 makes that many of the next
+ * tensor-core sweep launches stall on purpose: the control thread of their
+ * first CTA issues no copy and no MMA, so that CTA's first wait runs out with
+ * nothing in flight.  Process-wide, not thread-safe; for tests only. */
+rr_status rr_debug_waits(unsigned tries, int stall_launches);
 
 /* Number of problems (shifts) and precision of a factors object. */
 rr_status rr_factors_dims(const rr_factors* f, int* nshift, int* prec);

@@ -122,6 +122,7 @@ SIGNATURES = {
     "rr_batch_set_shifts": (_I, [_P, ctypes.POINTER(ctypes.c_double)]),
     "rr_batch_describe": (_I, [_P, ctypes.POINTER(rr_batch_desc)]),
     "rr_batch_destroy": (_I, [_P]),
+    "rr_debug_waits": (_I, [ctypes.c_uint, _I]),
     "rr_launch_count": (ctypes.c_longlong, []),
     "rr_profile_start": (_I, [ctypes.c_uint]),
     "rr_profile_read": (_I, [_I, ctypes.POINTER(ctypes.c_double),
@@ -165,6 +166,56 @@ def _dptr(t) -> int:
     return t.data_ptr()
 
 
+def _check_meta(name, t, dtype, shape):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def _check_place(name, t, device=None):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous CUDA tensor")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name}: on cuda:{t.device.index}, expected cuda:{device}")
+
+
+def _check_tensor(name, t, dtype, shape, device=None):
+    """Raise ValueError unless t is a contiguous CUDA tensor of the given
+    dtype and shape (on the given device ordinal when not None).  The C
+    library trusts the sizes it is given, so a short or mistyped buffer must
+    be caught here, before a kernel reads or writes past its end."""
+    _check_meta(name, t, dtype, shape)
+    _check_place(name, t, device)
+
+
+def _check_block_pair(x, y, F, n, device=None):
+    """x, y: distinct complex128 block vectors [F, n, k]; returns k."""
+    import torch
+    if not isinstance(x, torch.Tensor) or x.dim() != 3:
+        raise ValueError("x: expected a [F, N, k] tensor")
+    k = int(x.shape[2])
+    _check_meta("x", x, torch.complex128, (F, n, k))
+    _check_meta("y", y, torch.complex128, (F, n, k))
+    _check_place("x", x, device)
+    _check_place("y", y, device)
+    if x.data_ptr() == y.data_ptr():
+        raise ValueError("x and y must be distinct buffers")
+    return k
+
+
+def _operator_device(h) -> int:
+    """Device ordinal recorded with an operator handle by Operator (None for
+    a bare handle)."""
+    return _OP_DEVICE.get(int(h.value if hasattr(h, "value") else h))
+
+
+_OP_DEVICE: dict = {}
+
+
 def _stream_ptr(stream):
     if stream is None:
         return None
@@ -202,11 +253,13 @@ def rr_create_operator(grid, rho, u, v, weights=None, device: int = 0):
     h = ctypes.c_void_p()
     _check(lib.rr_create_operator(ctypes.byref(g), ctypes.byref(fl), w, int(device),
                                   ctypes.byref(h)))
+    _OP_DEVICE[int(h.value)] = int(device)
     return h
 
 
 def rr_destroy_operator(h):
     if h:
+        _OP_DEVICE.pop(int(h.value if hasattr(h, "value") else h), None)
         _check(load().rr_destroy_operator(h))
 
 
@@ -216,20 +269,32 @@ def rr_operator_dims(h):
     return tuple(v.value for v in vals)
 
 
+def _apply_args(h, shifts, x, y):
+    s = np.asarray(shifts, dtype=np.complex128).ravel()
+    n = rr_operator_dims(h)[0]
+    F = s.size
+    if F < 1:
+        raise ValueError("at least one shift")
+    k = _check_block_pair(x, y, F, n, _operator_device(h))
+    return s, F, k
+
+
 def rr_apply(h, shifts, x, y, adjoint=False, stream=None):
-    F, _, k = x.shape
-    _check(load().rr_apply(h, F, _shift_array(shifts), k, int(adjoint), _dptr(x),
+    s, F, k = _apply_args(h, shifts, x, y)
+    _check(load().rr_apply(h, F, _shift_array(s), k, int(adjoint), _dptr(x),
                            _dptr(y), _stream_ptr(stream)))
 
 
 def rr_apply_static(h, shifts, x, y, adjoint=False, stream=None):
     """rr_apply without any device allocation (shifts staged in a fixed array)."""
-    F, _, k = x.shape
-    _check(load().rr_apply_static(h, F, _shift_array(shifts), k, int(adjoint), _dptr(x),
+    s, F, k = _apply_args(h, shifts, x, y)
+    _check(load().rr_apply_static(h, F, _shift_array(s), k, int(adjoint), _dptr(x),
                                   _dptr(y), _stream_ptr(stream)))
 
 
 def rr_phi(h, phi, stream=None):
+    import torch
+    _check_tensor("phi", phi, torch.float64, (rr_operator_dims(h)[0],), _operator_device(h))
     _check(load().rr_phi(h, _dptr(phi), _stream_ptr(stream)))
 
 
@@ -241,17 +306,54 @@ def rr_factor(h, shifts, precision="fp64", stream=None):
     if st != RR_OK and out:
         load().rr_destroy_factors(out)
     _check(st)
+    n, _, _, nx, ny = rr_operator_dims(h)
+    _FA_DIMS[int(out.value)] = (s.size, n, _operator_device(h), nx * ny)
     return out
 
 
 def rr_destroy_factors(h):
     if h:
+        _FA_DIMS.pop(int(h.value if hasattr(h, "value") else h), None)
         _check(load().rr_destroy_factors(h))
+
+
+# factors handle -> (F, N, device ordinal) recorded by rr_factor
+_FA_DIMS: dict = {}
+
+
+def _fa_dims(h):
+    d = _FA_DIMS.get(int(h.value if hasattr(h, "value") else h))
+    if d is None:
+        raise ValueError("unknown factors handle (not created by rr_factor)")
+    return d[:3]
+
+
+def _check_blocks(h, k, **tensors):
+    """Every named tensor is a complex128 block vector [F, N, k] of the
+    factors h (or, for names starting with 'sigma', float64 [F, k])."""
+    import torch
+    F, n, dev = _fa_dims(h)
+    for name, t in tensors.items():
+        if t is None:
+            continue
+        if name.startswith("sigma"):
+            _check_meta(name, t, torch.float64, (F, k))
+        else:
+            _check_meta(name, t, torch.complex128, (F, n, k))
+    for name, t in tensors.items():
+        if t is not None:
+            _check_place(name, t, dev)
+    return F, n
 
 
 def rr_solve(h, b, x, adjoint=False, refine_tol=1e-10, max_refine=10):
     info = rr_info()
-    _, _, k = b.shape
+    if b.dim() != 3:
+        raise ValueError("b: expected a [F, N, k] tensor")
+    k = int(b.shape[2])
+    _check_blocks(h, k, b=b, x=x)
+    if b.data_ptr() == x.data_ptr():
+        raise ValueError("b and x must be distinct buffers")
     st = load().rr_solve(h, k, int(adjoint), _dptr(b), _dptr(x), float(refine_tol),
                          int(max_refine), ctypes.byref(info))
     return st, info
@@ -259,8 +361,17 @@ def rr_solve(h, b, x, adjoint=False, refine_tol=1e-10, max_refine=10):
 
 def rr_sketch(h, k, seeds, phi, V, sigma_halko, refine_tol=1e-10, max_refine=10,
               omega_kind="gaussian", density=1.0 / 3.0, power_iters=0):
+    import torch
     info = rr_info()
+    F, n, dev = _fa_dims(h)
     sd = np.asarray(seeds, dtype=np.uint64).ravel()
+    if sd.size != F:
+        raise ValueError(f"seeds: {sd.size} values, expected one per shift ({F})")
+    if phi is not None:
+        _check_meta("phi", phi, torch.float64, (n,))
+    _check_blocks(h, int(k), V=V, sigma_halko=sigma_halko)
+    if phi is not None:
+        _check_place("phi", phi, dev)
     arr = (ctypes.c_uint64 * sd.size)(*[int(x) for x in sd])
     phip = None if phi is None else _dptr(phi)
     if omega_kind == "gaussian" and power_iters == 0:
@@ -277,14 +388,25 @@ def rr_sketch(h, k, seeds, phi, V, sigma_halko, refine_tol=1e-10, max_refine=10,
 
 def rr_modes(h, k, V, U, sigma, orthogonalize=False, refine_tol=1e-10, max_refine=10):
     info = rr_info()
+    _check_blocks(h, int(k), V=V, U=U, sigma=sigma)
+    if V.data_ptr() == U.data_ptr():
+        raise ValueError("V and U must be distinct buffers")
     st = load().rr_modes(h, int(k), _dptr(V), _dptr(U), _dptr(sigma), int(orthogonalize),
                          float(refine_tol), int(max_refine), ctypes.byref(info))
     return st, info
 
 
 def rr_gain_grad(h, J, U, V, sigma, grad, refine_tol=1e-10, max_refine=10):
+    import torch
     info = rr_info()
-    k = U.shape[2]
+    if U.dim() != 3:
+        raise ValueError("U: expected a [F, N, k] tensor")
+    k = int(U.shape[2])
+    _fa_dims(h)
+    npts = _FA_DIMS[int(h.value if hasattr(h, "value") else h)][3]
+    _check_meta("grad", grad.reshape(-1), torch.float64, (3 * npts,))
+    _check_blocks(h, k, U=U, V=V, sigma=sigma)
+    _check_place("grad", grad, _fa_dims(h)[2])
     st = load().rr_gain_grad(h, int(k), int(J), _dptr(U), _dptr(V), _dptr(sigma),
                              float(refine_tol), int(max_refine), _dptr(grad),
                              ctypes.byref(info))
@@ -292,7 +414,17 @@ def rr_gain_grad(h, J, U, V, sigma, grad, refine_tol=1e-10, max_refine=10):
 
 
 def rr_refactor(h, shifts):
-    _check(load().rr_refactor(h, _shift_array(shifts)))
+    s = np.asarray(shifts, dtype=np.complex128).ravel()
+    if s.size != _fa_dims(h)[0]:
+        raise ValueError("rr_refactor needs one shift per problem of the factors")
+    _check(load().rr_refactor(h, _shift_array(s)))
+
+
+def rr_debug_waits(tries: int = 0, stall_launches: int = 0):
+    """Bounded-wait diagnostics (tests of RR_ERR_TIMEOUT): polls per wait
+    (0 = default) and the number of next tensor-core sweep launches whose
+    first CTA stalls on purpose."""
+    _check(load().rr_debug_waits(int(tries), int(stall_launches)))
 
 
 def rr_launch_count() -> int:
@@ -313,8 +445,19 @@ def rr_profile_read(cls):
     return ms.value, n.value
 
 
+def _check_omega(sd, n, k, phi, omega):
+    import torch
+    _check_meta("omega", omega, torch.complex128, (sd.size, int(n), int(k)))
+    if phi is not None:
+        _check_meta("phi", phi, torch.float64, (int(n),))
+    _check_place("omega", omega)
+    if phi is not None:
+        _check_place("phi", phi, omega.device.index)
+
+
 def rr_gaussian(seeds, n, k, phi, omega, stream=None):
     sd = np.asarray(seeds, dtype=np.uint64).ravel()
+    _check_omega(sd, n, k, phi, omega)
     arr = (ctypes.c_uint64 * sd.size)(*[int(x) for x in sd])
     _check(load().rr_gaussian(sd.size, int(n), int(k), arr,
                               None if phi is None else _dptr(phi), _dptr(omega),
@@ -323,6 +466,7 @@ def rr_gaussian(seeds, n, k, phi, omega, stream=None):
 
 def rr_test_matrix(seeds, n, k, phi, omega, kind="gaussian", density=1.0 / 3.0, stream=None):
     sd = np.asarray(seeds, dtype=np.uint64).ravel()
+    _check_omega(sd, n, k, phi, omega)
     arr = (ctypes.c_uint64 * sd.size)(*[int(x) for x in sd])
     kind = OMEGA_KINDS[kind] if isinstance(kind, str) else int(kind)
     _check(load().rr_test_matrix(sd.size, int(n), int(k), arr,

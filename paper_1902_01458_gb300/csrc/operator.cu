@@ -7,6 +7,8 @@
 // 9 x q x q coefficients of the linearised equations.
 #include <algorithm>
 
+#include <mutex>
+
 #include "rr_internal.cuh"
 
 namespace {
@@ -291,37 +293,49 @@ apply_ell_kernel(OpView op, const double2* __restrict__ shifts, int k,
 constexpr int kEllWidths[] = {4, 6, 8, 10, 13, 16, 20, 27};
 
 // ELL copy of the stencil: the widest row, then every row's nonzero entries
-// in slot order, padded with zero entries on the row itself.
-__global__ void ell_count_kernel(OpView op, int* wmax) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= op.n) return;
-  const double* cf = op.coef + (size_t)n * op.S;
-  int cnt = 0;
-  for (int e = 0; e < op.S; ++e) cnt += cf[e] != 0.0 ? 1 : 0;
-  atomicMax(wmax, cnt);
-}
-
-__global__ void ell_fill_kernel(OpView op, int W, double* __restrict__ val, int* __restrict__ col) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= op.n) return;
+// in slot order, padded with zero entries on the row itself.  Both kernels
+// walk the entries of a row with the same rule (in-grid neighbour, nonzero
+// coefficient), so the counted width always holds the filled row; a row that
+// would not fit anyway sets *overflow instead of losing entries.
+template <typename Visit>
+__device__ __forceinline__ void ell_row_entries(const OpView& op, int n, Visit&& visit) {
   const int q = op.q, pt = n / q;
   const int ix = pt / op.ny, iy = pt - ix * op.ny;
   const double* cf = op.coef + (size_t)n * op.S;
-  double* v = val + (size_t)n * W;
-  int* c = col + (size_t)n * W;
-  int t = 0;
   for (int sl = 0; sl < 9; ++sl) {
     const int jx = ix + sl / 3 - 1;
     const int jy = nbr_y(iy, sl % 3 - 1, op.ny, op.periodic);
     if (jx < 0 || jx >= op.nx || jy < 0) continue;
     for (int cp = 0; cp < q; ++cp) {
       const double a = cf[sl * q + cp];
-      if (a == 0.0 || t >= W) continue;
-      v[t] = a;
-      c[t] = (jx * op.ny + jy) * q + cp;
-      ++t;
+      if (a != 0.0) visit(a, (jx * op.ny + jy) * q + cp);
     }
   }
+}
+
+__global__ void ell_count_kernel(OpView op, int* wmax) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= op.n) return;
+  int cnt = 0;
+  ell_row_entries(op, n, [&](double, int) { ++cnt; });
+  atomicMax(wmax, cnt);
+}
+
+__global__ void ell_fill_kernel(OpView op, int W, double* __restrict__ val, int* __restrict__ col,
+                                int* overflow) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= op.n) return;
+  double* v = val + (size_t)n * W;
+  int* c = col + (size_t)n * W;
+  int t = 0;
+  ell_row_entries(op, n, [&](double a, int m) {
+    if (t < W) {
+      v[t] = a;
+      c[t] = m;
+    }
+    ++t;
+  });
+  if (t > W) atomicExch(overflow, 1);
   for (; t < W; ++t) {
     v[t] = 0.0;
     c[t] = n;
@@ -351,30 +365,47 @@ __global__ void round_coef_kernel(const double* __restrict__ in, float* __restri
 static dim3 apply_grid(const OpDev& d, int F, int k);
 
 rr_status build_ell(OpDev& d) {
-  int* wdev = nullptr;
-  RR_CUDA(cudaMalloc(&wdev, sizeof(int)));
+  int* wdev = nullptr;  // [0] widest row, [1] overflow flag of the fill
+  RR_CUDA(cudaMalloc(&wdev, 2 * sizeof(int)));
   const int blocks = (d.n + 255) / 256;
   int W = 0;
-  cudaError_t e = cudaMemset(wdev, 0, sizeof(int));
+  cudaError_t e = cudaMemset(wdev, 0, 2 * sizeof(int));
   if (e == cudaSuccess) {
     prof_count(1);
     ell_count_kernel<<<blocks, 256>>>(view(d), wdev);
     e = cudaMemcpy(&W, wdev, sizeof(int), cudaMemcpyDeviceToHost);
   }
-  cudaFree(wdev);
-  if (e != cudaSuccess) return cuda_status(e, "ELL stencil width");
-  d.ell_w = kEllWidths[sizeof(kEllWidths) / sizeof(int) - 1];
+  if (e != cudaSuccess) {
+    cudaFree(wdev);
+    return cuda_status(e, "ELL stencil width");
+  }
+  constexpr int kWidest = kEllWidths[sizeof(kEllWidths) / sizeof(int) - 1];
+  if (W > kWidest) {
+    cudaFree(wdev);
+    set_error("ELL stencil row wider than the widest compiled apply kernel");
+    return RR_ERR_ARG;
+  }
+  d.ell_w = kWidest;
   for (int w : kEllWidths)
     if (w >= W) {
       d.ell_w = w;
       break;
     }
-  RR_CUDA(cudaMalloc(&d.ell_val, (size_t)d.n * d.ell_w * sizeof(double)));
-  RR_CUDA(cudaMalloc(&d.ell_col, (size_t)d.n * d.ell_w * sizeof(int)));
-  prof_count(1);
-  ell_fill_kernel<<<blocks, 256>>>(view(d), d.ell_w, d.ell_val, d.ell_col);
-  RR_CUDA(cudaGetLastError());
-  RR_CUDA(cudaDeviceSynchronize());
+  e = cudaMalloc(&d.ell_val, (size_t)d.n * d.ell_w * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d.ell_col, (size_t)d.n * d.ell_w * sizeof(int));
+  int overflow = 0;
+  if (e == cudaSuccess) {
+    prof_count(1);
+    ell_fill_kernel<<<blocks, 256>>>(view(d), d.ell_w, d.ell_val, d.ell_col, wdev + 1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&overflow, wdev + 1, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(wdev);
+  if (e != cudaSuccess) return cuda_status(e, "ELL stencil copy");
+  if (overflow) {
+    set_error("ELL stencil copy: a row has more entries than the counted width");
+    return RR_ERR_ARG;
+  }
   return RR_OK;
 }
 
@@ -455,7 +486,10 @@ static __device__ __align__(256) double2 g_apply_static_shifts[RR_APPLY_STATIC_M
 
 namespace {
 constexpr int kMaxDevices = 64;
+// Device address of g_apply_static_shifts per device ordinal, looked up once
+// under g_static_mutex.  A cudaDeviceReset of that device invalidates it.
 double2* g_static_shift_ptr[kMaxDevices] = {nullptr};
+std::mutex g_static_mutex;
 }  // namespace
 
 extern "C" rr_status rr_apply_static(rr_operator* op, int nshift, const double* shifts, int k,
@@ -481,26 +515,39 @@ extern "C" rr_status rr_apply_static(rr_operator* op, int nshift, const double* 
     set_error("rr_apply_static: device ordinal out of range");
     return RR_ERR_ARG;
   }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // every call copies the shifts from pageable host memory and synchronises
+  // its stream, neither of which a capturing stream allows
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  RR_CUDA(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone) {
+    set_error("rr_apply_static: the stream is capturing (not supported)");
+    return RR_ERR_ARG;
+  }
   int prev = -1;
   RR_CUDA(cudaGetDevice(&prev));
   if (prev != dev) RR_CUDA(cudaSetDevice(dev));
   rr_status s = RR_OK;
   // one-time set-up on this device: the host cannot use the symbol itself as
   // a device address, so fetch the address with the device current
-  if (g_static_shift_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_apply_static_shifts);
-    if (e != cudaSuccess) s = cuda_status(e, "rr_apply_static: cudaGetSymbolAddress");
-    else g_static_shift_ptr[dev] = static_cast<double2*>(p);
+  double2* shift_dev = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (g_static_shift_ptr[dev] == nullptr) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_apply_static_shifts);
+      if (e != cudaSuccess) s = cuda_status(e, "rr_apply_static: cudaGetSymbolAddress");
+      else g_static_shift_ptr[dev] = static_cast<double2*>(p);
+    }
+    shift_dev = g_static_shift_ptr[dev];
   }
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (s == RR_OK) {
-    cudaError_t e = cudaMemcpyAsync(g_static_shift_ptr[dev], shifts, nshift * sizeof(double2),
+    cudaError_t e = cudaMemcpyAsync(shift_dev, shifts, nshift * sizeof(double2),
                                     cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) s = cuda_status(e, "rr_apply_static: shift copy");
   }
   if (s == RR_OK)
-    s = launch_apply(op->d, nshift, g_static_shift_ptr[dev], k, adjoint,
+    s = launch_apply(op->d, nshift, shift_dev, k, adjoint,
                      static_cast<const double2*>(x), static_cast<double2*>(y), st);
   if (s == RR_OK) {
     cudaError_t e = cudaStreamSynchronize(st);

@@ -13,7 +13,30 @@ long long g_class_launches[PROF_N] = {0};
 long long g_launches = 0;
 
 int g_suspended = 0;
+
+// bounded-wait diagnostics (rr_debug_waits)
+constexpr uint32_t kDefaultWaitTries = 1u << 22;
+uint32_t g_wait_tries = kDefaultWaitTries;
+int g_stall_launches = 0;
 }  // namespace
+
+uint32_t wait_tries() { return g_wait_tries; }
+
+int take_stall() {
+  if (g_stall_launches <= 0) return 0;
+  --g_stall_launches;
+  return 1;
+}
+
+extern "C" rr_status rr_debug_waits(unsigned tries, int stall_launches) {
+  if (stall_launches < 0) {
+    set_error("rr_debug_waits: stall_launches must be >= 0");
+    return RR_ERR_ARG;
+  }
+  g_wait_tries = tries == 0 ? kDefaultWaitTries : tries;
+  g_stall_launches = stall_launches;
+  return RR_OK;
+}
 
 ProfSuspend::ProfSuspend() { ++g_suspended; }
 ProfSuspend::~ProfSuspend() { --g_suspended; }

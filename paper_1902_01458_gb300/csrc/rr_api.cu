@@ -249,7 +249,10 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
     RR_CUDA(cudaMemcpyAsync(&tc_err, fa->flag + F, sizeof(int), cudaMemcpyDeviceToHost, st));
     RR_CUDA(cudaStreamSynchronize(st));
     if (tc_err) {
-      g_err = "a tensor-core sweep kernel timed out waiting for its MMAs";
+      // reported once: the flag is cleared so the factors serve later solves
+      RR_CUDA(cudaMemsetAsync(fa->flag + F, 0, sizeof(int), st));
+      RR_CUDA(cudaStreamSynchronize(st));
+      g_err = "a tensor-core sweep kernel timed out in a bounded wait";
       return RR_ERR_TIMEOUT;
     }
     rel = 0.0;

@@ -270,5 +270,9 @@ struct ProfSuspend {
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
 void prof_count(int n);
+// bounded-wait diagnostics: polls before an mbarrier wait gives up, and
+// whether the next tensor-core sweep launch stalls (test-only, rr_debug_waits)
+uint32_t wait_tries();
+int take_stall();
 
 int num_sms(int device);

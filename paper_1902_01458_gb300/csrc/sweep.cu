@@ -463,8 +463,8 @@ __host__ __device__ constexpr size_t tc2_smem_bytes(int kp) {
          (size_t)TC2_STAGES * tc2_stage_bytes(kp);
 }
 
-__device__ __forceinline__ bool tc_poll(uint64_t* bar, uint32_t parity) {
-  return tc::mbar_wait(bar, parity, TC_WAIT_TRIES);
+__device__ __forceinline__ bool tc_poll(uint64_t* bar, uint32_t parity, uint32_t tries) {
+  return tc::mbar_wait(bar, parity, tries);
 }
 
 constexpr int TC2_CONV = 256;                 // converter threads (warps 0-7)
@@ -474,7 +474,7 @@ template <bool TRANS>
 __global__ void __launch_bounds__(TC2_THREADS, 1)
 sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp, int blk,
                  int nx, int nrt, int KS, int cpp, const float2* rhs, size_t rstride,
-                 float2* __restrict__ part, int F, int* err) {
+                 float2* __restrict__ part, int F, int* err, uint32_t tries, int stall) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t full_bar[TC2_STAGES];
   __shared__ uint64_t mma_bar[2];
@@ -519,14 +519,18 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
   const uint32_t tmem = tmem_base;
   const uint32_t set_cols = (uint32_t)(3 * N <= 128 ? 128 : 256);  // one accumulator set
 
-  // control thread: the stream of chunks of all this CTA's items
+  // control thread: the stream of chunks of all this CTA's items.  With
+  // stall set (a diagnostic of the bounded waits) the first CTA issues
+  // nothing at all, so its first wait runs out with no copy or MMA in flight.
+  const bool stalled = stall && blockIdx.x == 0;
   int p_item = 0, p_lc = 0, issued = 0, p_f = 0, p_rt = 0, p_ks = 0, p_len = 0;
+  int committed = 0;  // chunks whose MMAs have been committed (control thread)
   if (ctrl && my_items > 0) {
     item(0, p_f, p_rt, p_ks);
     p_len = item_len(p_ks);
   }
   auto issue_next = [&]() {
-    if (p_item >= my_items) return;
+    if (stalled || p_item >= my_items) return;
     const int m0 = (p_ks * cpp + p_lc) * TC2_KC;
     const int s = issued % TC2_STAGES;
     const uint32_t rhs_bytes = (uint32_t)(min(TC2_KC, b - m0) * k * 8);
@@ -571,8 +575,8 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
       const int s = g % TC2_STAGES, q = g & 1;
       bool ok = true;
       if (tid < TC2_CONV) {
-        ok = tc_poll(&full_bar[s], (g / TC2_STAGES) & 1);
-        if (ok && g >= 2) ok = tc_poll(&mma_bar[q], ((g - 2) >> 1) & 1);  // buffer q is free
+        ok = tc_poll(&full_bar[s], (g / TC2_STAGES) & 1, tries);
+        if (ok && g >= 2) ok = tc_poll(&mma_bar[q], ((g - 2) >> 1) & 1, tries);  // buffer q is free
         tc::fence_after_sync();
         unsigned char* A_hi = ops + q * buf_bytes;
         unsigned char* A_lo = A_hi + TC2_A_BYTES;
@@ -643,11 +647,12 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
           tc::mma_tf32(set + 2 * N, dA[q][1] + koff, dB[q][0] + koff, idesc_lo, acc);
         }
         tc::mma_commit(&mma_bar[q]);
+        ++committed;
       }
     }
     if (failed) break;
     // item done: wait for its last MMAs, then move the accumulator to its slot
-    bool ok = (tid < TC2_CONV) ? tc_poll(&mma_bar[(g - 1) & 1], ((g - 1) >> 1) & 1) : true;
+    bool ok = (tid < TC2_CONV) ? tc_poll(&mma_bar[(g - 1) & 1], ((g - 1) >> 1) & 1, tries) : true;
     failed = __syncthreads_or(ok ? 0 : 1) != 0;
     if (failed) break;
     tc::fence_after_sync();
@@ -676,9 +681,14 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
   }
   if (failed && ctrl) {
     atomicExch(err, 1);
-    // drain the copies still in flight before the CTA's shared memory goes
+    // drain the copies still in flight before the CTA's shared memory goes,
+    // and the last committed MMAs before their tensor memory is freed
     for (int qq = g; qq < issued; ++qq)
       tc::mbar_wait(&full_bar[qq % TC2_STAGES], (qq / TC2_STAGES) & 1, TC_WAIT_TRIES);
+    if (committed > 0) {
+      const int last = committed - 1;
+      tc::mbar_wait(&mma_bar[last & 1], (uint32_t)(last >> 1) & 1u, TC_WAIT_TRIES);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -755,7 +765,7 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
       prof_begin(PROF_SWEEP, st);
       sweep_tc2_kernel<TRANS><<<grid_x, TC2_THREADS, smem, st>>>(
           *tm, b, k, kp, blk, d.nx, nrt, KS, cpp, reinterpret_cast<const float2*>(rhs), rstride,
-          reinterpret_cast<float2*>(fa->Pbuf), F, fa->flag + F);
+          reinterpret_cast<float2*>(fa->Pbuf), F, fa->flag + F, wait_tries(), take_stall());
       const size_t total = (size_t)F * b * k;
       const int cblocks = (int)std::min<size_t>((total + 255) / 256, 8192);
       sweep_combine_kernel<EPI><<<cblocks, 256, 0, st>>>(

@@ -6,6 +6,8 @@ Tolerances (fixed by the method's accuracy targets): FP64 path sigma_j within
 subspaces within 1e-5 radians (largest principal angle).  Operator application
 and Omega are compared at rounding level.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -36,6 +38,10 @@ def _cases():
         ("ns-neumann-9x11", W.ns_grid(9, 11, neumann=W.PAPER_NEUMANN), "random"),
         ("advdiff-neumann-all", W.Grid(kind=W.KIND_ADVDIFF, nx=8, ny=9, x0=0, x1=2, y0=0,
                                        y1=3, re=5.0, neumann=(1, 1, 1, 1)), "random"),
+        # NS with a periodic y direction and Neumann x sides: the widest ELL rows
+        # (folded ghost coefficients, wrapped neighbours) against the oracle
+        ("ns-periodic-neumann-x", dataclasses.replace(W.ns_grid(10, 8), periodic_y=True,
+                                                      neumann=(1, 7, 0, 0)), "random"),
     ]
 
 

@@ -119,6 +119,73 @@ def test_ns_operator_is_second_order_consistent():
     assert 3.2 < ratio < 5.0, (e1, e2, ratio)
 
 
+def _ns_boundary_consistency_error(nx, ny):
+    """Consistency on every row, boundary rows included.  A bilinear base
+    flow makes the base-flow differences exact at every node (one-sided first
+    differences at the ends are exact on linear fields, the re-centred second
+    differences on quadratics), and perturbations that vanish at the ghost
+    nodes make the Dirichlet closure exact, so the first and last rows must
+    converge at second order like the interior ones."""
+    g = W.Grid(kind=W.KIND_NS2D, nx=nx, ny=ny, x0=0.0, x1=4.0, y0=-1.5,
+               y1=1.5, re=50.0, mach=0.5)
+    x, y = sy.symbols("x y", real=True)
+    R0 = 1 + 3 * x / 10 + y / 10 + x * y / 20
+    U0 = sy.Rational(1, 2) + 2 * x / 5 - 3 * y / 10 - x * y / 10
+    V0 = sy.Rational(1, 5) - 3 * x / 10 + y / 5 + x * y / 10
+    bump = sy.sin(sy.pi * x / 4) * sy.sin(sy.pi * (y + sy.Rational(3, 2)) / 3)
+    r1 = bump * sy.cos(4 * x / 5)
+    u1 = bump * sy.sin(y / 2 + sy.Rational(3, 10))
+    v1 = bump * sy.cos(2 * x / 5 + y / 5)
+    lin = _sym_ns_linearised(g, R0, U0, V0, r1, u1, v1, x, y)
+    X, Y = g.mesh()
+    f = lambda e: np.broadcast_to(sy.lambdify((x, y), e, "numpy")(X, Y),
+                                  X.shape).astype(float)
+    flow = W.BaseFlow(rho=f(R0), u=f(U0), v=f(V0))
+    qp = np.stack([f(r1), f(u1), f(v1)], axis=-1).ravel()
+    got = (op.assemble(g, flow) @ qp).reshape(nx, ny, 3)
+    want = np.stack([f(e) for e in lin], axis=-1)
+    err = np.abs(got - want)
+    edge = np.zeros((nx, ny), dtype=bool)
+    edge[[0, -1], :] = True
+    edge[:, [0, -1]] = True
+    return np.max(err[edge]), np.max(err), np.max(np.abs(want))
+
+
+def test_ns_boundary_rows_are_second_order_consistent():
+    e1, a1, scale = _ns_boundary_consistency_error(24, 20)
+    e2, a2, _ = _ns_boundary_consistency_error(48, 40)
+    assert a1 < 0.05 * scale
+    assert 3.2 < e1 / e2 < 5.0, (e1, e2)
+    assert 3.2 < a1 / a2 < 5.0, (a1, a2)
+
+
+def test_field_differences_exact_on_polynomials_at_every_node():
+    """The base-flow differences, end nodes included: the one-sided first
+    difference is exact on linear fields, the re-centred second difference on
+    quadratics, the cross difference on bilinear fields."""
+    g = W.ns_grid(9, 7)
+    X, Y = g.mesh()
+    lin = 0.3 + 1.7 * X - 0.9 * Y
+    d = op.field_derivatives(g, lin)
+    np.testing.assert_allclose(d["x"], 1.7, rtol=1e-12)
+    np.testing.assert_allclose(d["y"], -0.9, rtol=1e-12)
+    quad = 0.5 - 0.4 * X + 2.5 * X ** 2 + 0.7 * Y - 1.3 * Y ** 2
+    d = op.field_derivatives(g, quad)
+    np.testing.assert_allclose(d["xx"], 5.0, rtol=1e-10)
+    np.testing.assert_allclose(d["yy"], -2.6, rtol=1e-10)
+    bil = 0.2 + X - 0.5 * Y + 0.25 * X * Y
+    d = op.field_derivatives(g, bil)
+    np.testing.assert_allclose(d["xy"], 0.25, rtol=1e-12)
+    np.testing.assert_allclose(d["x"], 1 + 0.25 * Y, rtol=1e-12)
+    # a periodic direction: central differences wrap around
+    gp = W.Grid(kind=W.KIND_ADVDIFF, nx=5, ny=16, x0=0, x1=1, y0=0, y1=2 * np.pi,
+                re=1.0, periodic_y=True)
+    _, Yp = gp.mesh()
+    dp = op.field_derivatives(gp, np.sin(Yp))
+    h = gp.dy
+    np.testing.assert_allclose(dp["y"], np.cos(Yp) * np.sin(h) / h, rtol=1e-12, atol=1e-14)
+
+
 def _advdiff_consistency_error(nx, ny):
     g = W.Grid(kind=W.KIND_ADVDIFF, nx=nx, ny=ny, x0=0.0, x1=10.0, y0=-5.0,
                y1=5.0, re=100.0)
