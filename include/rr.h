@@ -408,6 +408,15 @@ rr_status rr_profile_read(int cls, double* ms, long long* launches);
  * nothing in flight.  Process-wide, not thread-safe; for tests only. */
 rr_status rr_debug_waits(unsigned tries, int stall_launches);
 
+/* Measured arithmetic peaks for roofline fractions (no counterpart in the
+ * paper).  Runs a microbenchmark whose operands stay on chip on `device` and
+ * returns the best of five timed launches (after a warm-up) in TFLOP/s:
+ * kind 0 tcgen05.mma kind::tf32 (128 x 256 tiles, FP32 accumulation in
+ * TMEM), 1 tcgen05.mma kind::f16 with BF16 operands, 2 FP64 FMA and 3 FP32
+ * FMA on the CUDA cores (2 flops per FMA).  Synchronous.  Errors:
+ * RR_ERR_ARG, RR_ERR_TIMEOUT, RR_ERR_CUDA. */
+rr_status rr_measure_peak(int kind, int device, double* tflops);
+
 /* Number of problems (shifts) and precision of a factors object. */
 rr_status rr_factors_dims(const rr_factors* f, int* nshift, int* prec);
 

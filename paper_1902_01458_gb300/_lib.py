@@ -123,6 +123,7 @@ SIGNATURES = {
     "rr_batch_describe": (_I, [_P, ctypes.POINTER(rr_batch_desc)]),
     "rr_batch_destroy": (_I, [_P]),
     "rr_debug_waits": (_I, [ctypes.c_uint, _I]),
+    "rr_measure_peak": (_I, [_I, _I, ctypes.POINTER(ctypes.c_double)]),
     "rr_launch_count": (ctypes.c_longlong, []),
     "rr_profile_start": (_I, [ctypes.c_uint]),
     "rr_profile_read": (_I, [_I, ctypes.POINTER(ctypes.c_double),
@@ -425,6 +426,17 @@ def rr_debug_waits(tries: int = 0, stall_launches: int = 0):
     (0 = default) and the number of next tensor-core sweep launches whose
     first CTA stalls on purpose."""
     _check(load().rr_debug_waits(int(tries), int(stall_launches)))
+
+
+PEAK_KINDS = {"tf32": 0, "bf16": 1, "fp64": 2, "fp32": 3}
+
+
+def rr_measure_peak(kind: str, device: int = 0) -> float:
+    """Measured TFLOP/s of one arithmetic unit (tcgen05 TF32 / BF16 MMA, FP64 /
+    FP32 FMA) on the device, from an on-chip microbenchmark."""
+    v = ctypes.c_double()
+    _check(load().rr_measure_peak(PEAK_KINDS[kind], int(device), ctypes.byref(v)))
+    return v.value
 
 
 def rr_launch_count() -> int:

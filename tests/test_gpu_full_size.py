@@ -6,14 +6,23 @@ bench times.
   LU runs at this size in seconds per frequency, so sigma, sigma_halko
   (1e-9 relative) and the mode subspaces (1e-5 rad) are compared directly.
 * 512 x 256 (N = 393,216, block 768), FP32 factors with FP64 refinement,
-  k = 32, the 64 frequencies of one bench step in one batch: the oracle's LU
-  is too slow here, so sampled outputs are checked against what the oracle
-  computes one by one -- its test matrix entries, and its sparse operator
-  applied to the recovered modes (A (sigma_j u_j) = v_j, the recovery
-  identity of Eq. 8 with identity weights) -- plus properties that hold at
-  any size (orthonormal V, sorted gains, sigma_1 >= sigma_1^Halko), and the
-  FP64 GPU path on one frequency (1e-6 relative, the mixed-precision bar).
+  k = 32, the 64 frequencies of one bench step in one batch: two of them (the
+  lowest frequency and the first above 3) against the oracle's Algorithm 1
+  with a banded LAPACK LU at full size (about 15 GB of host memory and a
+  minute or two each): sigma_1..sigma_32 and sigma_halko within 1e-6
+  relative, the mode subspaces within 1e-5 rad.  For every sampled frequency
+  also what the oracle computes one by one -- its test matrix entries, and
+  its sparse operator applied to the recovered modes (A (sigma_j u_j) = v_j,
+  the recovery identity of Eq. 8 with identity weights) -- plus properties
+  that hold at any size (orthonormal V, sorted gains, sigma_1 >=
+  sigma_1^Halko), and the FP64 GPU path on one frequency (1e-6 relative).
+* The differentiation workload at its size (256 x 128, 16 frequencies,
+  k = 16, chunks of 4): the autograd gradient against central differences
+  (h = 1e-6) of the objective on the first 4 of its 64 random directions.
 """
+import os
+import time
+
 import numpy as np
 import pytest
 
@@ -76,6 +85,9 @@ def test_mixed_workload_at_full_size_in_the_bench_configuration(env):
     for info in (i1, i2):
         assert info["refine_residual"] <= 1e-10 or info["refine_stagnated"]
     sig_h, sh_h = sig.cpu().numpy(), sh.cpu().numpy()
+    f_hi = int(np.argmax(wl.omegas > 3.0))
+    V_h = {f: V[f].cpu().numpy() for f in (0, f_hi)}
+    U_h = {f: U[f].cpu().numpy() for f in (0, f_hi)}
     assert np.all(np.diff(sig_h, axis=1) <= 0) and np.all(sh_h > 0)
     assert np.all(sig_h[:, 0] >= sh_h[:, 0] * (1 - 1e-9))
     L = op.assemble(g, flow)
@@ -91,6 +103,25 @@ def test_mixed_workload_at_full_size_in_the_bench_configuration(env):
     fa.close()
     del V, U
 
+    # the oracle's Algorithm 1 (banded LAPACK LU) at full size on two of the
+    # batch's frequencies, element by element
+    host_bytes = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    print(f"host memory {host_bytes / 2**30:.0f} GiB")
+    if host_bytes < 48 * 2 ** 30:
+        pytest.skip(f"host memory {host_bytes / 2**30:.0f} GiB: the banded oracle needs ~15 GB")
+    phi_h = phi.cpu().numpy()
+    for f in (0, f_hi):
+        t0 = time.perf_counter()
+        ref = rs.randomized(L, shifts[f], k, seeds[f], phi=phi_h, method="banded")
+        print(f"oracle frequency {f} (omega {wl.omegas[f]:.3f}): {time.perf_counter() - t0:.1f} s; "
+              f"max sigma rel err {np.max(np.abs(sig_h[f] - ref.sigma) / ref.sigma):.2e}")
+        np.testing.assert_allclose(sig_h[f], ref.sigma, rtol=1e-6)
+        np.testing.assert_allclose(sh_h[f], ref.sigma_halko, rtol=1e-6)
+        assert rs.principal_angle(V_h[f], ref.V) < 1e-5
+        assert rs.principal_angle(U_h[f], ref.U) < 1e-5
+        del ref
+    del V_h, U_h
+
     # the FP64 GPU path on the lowest frequency
     f64 = rr.Factors(o, shifts[:1], "fp64")
     V64, sh64, _ = f64.sketch(k, seeds[:1], phi)
@@ -98,3 +129,39 @@ def test_mixed_workload_at_full_size_in_the_bench_configuration(env):
     np.testing.assert_allclose(sig_h[0], sig64.cpu().numpy()[0], rtol=1e-6)
     np.testing.assert_allclose(sh_h[0], sh64.cpu().numpy()[0], rtol=1e-6)
     f64.close()
+
+
+def test_gradient_workload_at_full_size(env):
+    """The differentiation workload (256 x 128, 16 frequencies, k = 16, J = 3,
+    factors recomputed per 4-frequency chunk) through the autograd function:
+    the gradient against central differences with h = 1e-6 of the same
+    objective on the first 4 of the workload's 64 random directions.  FP64
+    factors (the difference quotient needs the objective to ~1e-12), two
+    subspace iterations.  A direction can be nearly orthogonal to the
+    gradient, so the error is measured against the rms directional
+    derivative (1e-5), as in the reduced test."""
+    torch, rr = env
+    from paper_1902_01458_gb300.autograd import gain_objective
+    wl = W.config_gradient()
+    g, base = wl.grid, wl.flow
+    seeds = [wl.seed0 + i for i in range(len(wl.omegas))]
+    kw = dict(grid=g, omegas=wl.omegas, k=wl.k, J=wl.J, seeds=seeds, chunk=wl.chunk,
+              precision="fp64", power_iters=2)
+    fields = [torch.tensor(a, dtype=torch.float64, requires_grad=True)
+              for a in (base.rho, base.u, base.v)]
+    val = gain_objective(*fields, **kw)
+    val.backward()
+    grad = np.stack([f.grad.numpy() for f in fields])
+    assert np.all(np.isfinite(grad)) and np.abs(grad).max() > 0
+    an, fd = [], []
+    for d in W.gradient_directions(wl, 4):
+        def at(t):
+            with torch.no_grad():
+                f = [torch.tensor(a + t * dd) for a, dd in zip((base.rho, base.u, base.v), d)]
+                return float(gain_objective(*f, **dict(kw, chunk=len(wl.omegas))))
+        fd.append((at(wl.h) - at(-wl.h)) / (2 * wl.h))
+        an.append(float(np.sum(grad * d)))
+    an, fd = np.array(an), np.array(fd)
+    scale = np.sqrt(np.mean(fd ** 2))
+    print("directional derivatives", an, fd, "rel err", np.abs(an - fd) / scale)
+    assert np.max(np.abs(an - fd)) <= 1e-5 * scale

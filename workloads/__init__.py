@@ -197,6 +197,37 @@ def config_small_ns(nx: int = 24, ny: int = 20, k: int = 8,
 
 
 @dataclasses.dataclass(frozen=True)
+class GradientWorkload:
+    grid: Grid
+    flow: BaseFlow
+    omegas: np.ndarray      # real frequencies; shift s = i * omega
+    k: int                  # sketch columns
+    J: int                  # objective: sum over omega of sum_{j<J} sigma_j^2
+    chunk: int              # frequencies per factorisation chunk
+    seed0: int              # Omega seed of frequency j is seed0 + j
+    h: float                # central-difference step
+    ndir: int               # random base-flow directions
+    dir_seed: int           # generator seed of the directions
+
+
+def config_gradient() -> GradientWorkload:
+    """Differentiation workload: d(sum_omega sum_{j<=3} sigma_j^2)/d(rho, U, V)
+    on the 256x128 NS grid about the shear-bubble flow, 16 frequencies
+    log-spaced in [0.1, 5], k = 16, factors per 4-frequency chunk, checked by
+    central differences (h = 1e-6) on 64 standard-normal field directions."""
+    g = ns_grid(256, 128)
+    return GradientWorkload(g, shear_bubble_flow(g), log_omegas(16), 16, 3, 4, 1000,
+                            1e-6, 64, 77)
+
+
+def gradient_directions(wl: GradientWorkload, n: int | None = None) -> np.ndarray:
+    """The first n (default all) random directions [n, 3, nx, ny]."""
+    rng = np.random.default_rng(wl.dir_seed)
+    n = wl.ndir if n is None else n
+    return rng.standard_normal((n, 3, wl.grid.nx, wl.grid.ny))
+
+
+@dataclasses.dataclass(frozen=True)
 class BatchProblem:
     nx: int
     ny: int
