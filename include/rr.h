@@ -54,13 +54,23 @@ typedef enum {
 
 /* Arithmetic of the block factorisation and the block sweeps.  FP64 runs
  * everything in complex double.  FP32 stores the factors in complex float,
- * runs the sweep products on the tensor cores (tcgen05 kind::tf32 with each
- * operand split into a TF32 part and its remainder: FP32-level products,
- * FP32 accumulation) and wins accuracy back by iterative refinement against
- * an FP64 residual.  FP32_SIMT is the same with every product on the FP32
- * CUDA cores.  QR, SVD, norms and the refinement residual stay FP64 in every
- * mode. */
-typedef enum { RR_FP64 = 0, RR_FP32 = 1, RR_FP32_SIMT = 2 } rr_precision;
+ * runs the factorisation's updates and the sweep products on the tensor
+ * cores (tcgen05 kind::tf32 with each operand split into a TF32 part and its
+ * remainder, hi.hi + hi.lo + lo.hi: FP32-level products, FP32 accumulation)
+ * and wins accuracy back by iterative refinement against an FP64 residual.
+ * FP32_BF16X3 and FP32_BF16X6 are the same with the operands split into
+ * BF16 pieces on tcgen05 kind::f16: two pieces and three products (about 16
+ * bits of each product) or three pieces and six products (hi.hi, hi.mid,
+ * mid.hi, hi.lo, mid.mid, lo.hi: FP32-level).  FP32_SIMT is FP32 with every
+ * product on the FP32 CUDA cores.  QR, SVD, norms and the refinement
+ * residual stay FP64 in every mode. */
+typedef enum {
+  RR_FP64 = 0,
+  RR_FP32 = 1,
+  RR_FP32_SIMT = 2,
+  RR_FP32_BF16X3 = 3,
+  RR_FP32_BF16X6 = 4
+} rr_precision;
 
 /* Operator kinds (q = unknowns per grid point). */
 enum { RR_ADVDIFF_SCALAR = 1, RR_ISO_NS2D = 3 };

@@ -20,7 +20,7 @@ RR_OK = 0
 STATUS = {0: "RR_OK", 1: "RR_ERR_ARG", 2: "RR_ERR_NOMEM", 3: "RR_ERR_SINGULAR",
           4: "RR_ERR_NOCONV", 5: "RR_ERR_RANK", 6: "RR_ERR_TIMEOUT",
           7: "RR_ERR_CUDA", 8: "RR_ERR_UNSUPPORTED"}
-PRECISION = {"fp64": 0, "fp32": 1, "fp32_simt": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32_simt": 2, "fp32_bf16x3": 3, "fp32_bf16x6": 4}
 ADVDIFF, NS2D = 1, 3
 
 

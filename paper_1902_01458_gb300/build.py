@@ -14,7 +14,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librr.so")
 
 SOURCES = ["operator.cu", "factor.cu", "sweep.cu", "dense.cu", "rr_api.cu", "prof.cu", "grad.cu",
-           "batch.cu", "peak.cu"]
+           "batch.cu", "peak.cu", "factor_w.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-diag-suppress", "177", f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -347,7 +347,7 @@ rr_status tune(rr_batch* B) {
   // trailing-update tile shape per group, on the first columns
   for (auto& G : B->groups) {
     const OpDev& d = G.op->d;
-    if (B->prec != RR_FP32 || d.b < 128 || d.b % 8 != 0) continue;
+    if (!tc_prec(B->prec) || d.b < 128 || d.b % 8 != 0) continue;
     const int cols = std::min(d.nx, 6);
     G.fa->tune_update = 0;
     const float t_tc = time_factor_cols(G.fa, cols);
@@ -363,7 +363,7 @@ rr_status tune(rr_batch* B) {
   // K-split of each view's tensor-core sweep
   for (auto& G : B->groups)
     for (auto& v : G.views) {
-      if (B->prec != RR_FP32 || !v.fa->tma_ok || v.k % 2 != 0 || v.k > 32) continue;
+      if (!tc_prec(B->prec) || !v.fa->tma_ok || v.k % 2 != 0 || v.k > 32) continue;
       float best = INFINITY;
       int best_ks = 0;
       for (int ks = 0; ks <= 4; ++ks) {
@@ -411,7 +411,8 @@ extern "C" rr_status rr_batch_create(int nprob, const rr_problem* probs, rr_prec
   if (!out) return berr(RR_ERR_ARG, "rr_batch_create: null out");
   *out = nullptr;
   if (nprob < 1 || !probs) return berr(RR_ERR_ARG, "rr_batch_create: need at least one problem");
-  if (prec != RR_FP64 && prec != RR_FP32 && prec != RR_FP32_SIMT)
+  if (prec != RR_FP64 && prec != RR_FP32 && prec != RR_FP32_SIMT && prec != RR_FP32_BF16X3 &&
+      prec != RR_FP32_BF16X6)
     return berr(RR_ERR_ARG, "rr_batch_create: unknown precision");
   rr_batch_opts o{1, 1e-10, 10, 0, 0};
   if (opts) o = *opts;

@@ -826,7 +826,7 @@ rr_status factor_impl(rr_factors* fa) {
   // and b >= 128 (the TMA map of M) update on the tensor cores;
   // RR_FP32_SIMT and FP64 on the CUDA cores
   constexpr bool tc_shape = std::is_same<T, float>::value && NB == 32;
-  const bool use_tc = tc_shape && fa->prec == RR_FP32 && b % 8 == 0 && b >= UTC_RT &&
+  const bool use_tc = tc_shape && tc_prec(fa->prec) && b % 8 == 0 && b >= UTC_RT &&
                       fa->tma_m_ok && fa->tune_update != 1;
   if (use_tc)
     RR_CUDA(cudaFuncSetAttribute(gj_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -920,7 +920,21 @@ int factor_panel_width(int prec, int b) {
   return prec == RR_FP64 ? panel_nb<double>(b) : panel_nb<float>(b);
 }
 
+rr_status launch_schur_f32(rr_factors* fa, int i, cudaStream_t st) {
+  const OpDev& d = fa->op->d;
+  const int b = d.b;
+  float2* X = reinterpret_cast<float2*>(fa->X);
+  dim3 gs((b + SCHUR_ROWS - 1) / SCHUR_ROWS, fa->F);
+  prof_begin(PROF_SCHUR, st);
+  schur_kernel<float><<<gs, SCHUR_THREADS, 0, st>>>(view(d), fa->shifts, i, i > 0 ? X : nullptr,
+                                                   (size_t)b * b, reinterpret_cast<float2*>(fa->M));
+  prof_end(PROF_SCHUR, st);
+  RR_CUDA(cudaGetLastError());
+  return RR_OK;
+}
+
 rr_status launch_factor(rr_factors* fa) {
   if (fa->prec == RR_FP64) return factor_dispatch<double>(fa);
+  if (factor_wide_ok(fa) && fa->tune_update != 1) return launch_factor_wide(fa);
   return factor_dispatch<float>(fa);
 }

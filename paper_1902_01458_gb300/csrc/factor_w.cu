@@ -1,0 +1,747 @@
+// Wide block factorisation of the Schur blocks for FP32 factors: the explicit
+// inverse G_i = S_i^{-1} of Sec. III.A's one-factorisation-per-shift scheme
+// (S_0 = D_0, X_i = G_i C_i, S_{i+1} = D_{i+1} - A_{i+1} X_i), formed by
+// Gauss-Jordan elimination with partial pivoting in two levels so that the
+// bulk of the work is a rank-128 complex update on the tensor cores.
+//
+// Pivoting is implicit: rows are never moved.  Column j is eliminated with
+// the pivot row p_j (the largest |.| among rows not yet pivoted, lowest row on
+// ties) by the elementary transformation E_j (row p_j scaled by 1/m_pj,
+// m_pj times it subtracted from every other row; column j then holds E_j's
+// column p_j, the in-place inverse).  After all b columns the work matrix is
+// M = Q^T S^{-1} Q^T with (Q x)_j = x_{p_j}, so S^{-1}[j, p_m] = M[p_j, m].
+//
+// Levels, for every slab of W = 128 columns [c0, c1):
+//   inner, per panel K of 32 columns:
+//     panel  : one CTA per problem holds the tall panel M[:, K] in registers
+//              (one row per thread) and applies the 32 eliminations to it,
+//              recording the pivot rows P;
+//     update : M[:, slab \ K] += (M[:, K] - I[:, P]) * M_old[P, slab \ K]
+//              (the transformations of K applied to the rest of the slab);
+//   outer:
+//     gather : B = M[P_slab, outside the slab] (the pivot rows, saved before
+//              they change);
+//     update : M[:, outside] += (M[:, slab] - I[:, P_slab]) * B, the composed
+//              transformation of the slab's 128 eliminations applied at once.
+// Both updates are one tensor-core kernel (gjw_gemm_kernel): a complex GEMM
+// C += A B with A read from M (minus the identity at the pivot rows) and B
+// from the gathered rows, as a real GEMM on tcgen05 with the operands split
+// into TF32 or BF16 pieces (FP32-level products, FP32 accumulation in TMEM).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "rr_internal.cuh"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int GW_W = 128;   // slab width (rank of the outer update)
+constexpr int GW_NB = 16;   // panel width (rank of the inner update)
+constexpr int GW_PANEL_MAX = 768;  // rows a panel CTA holds (one per thread)
+
+// ------------------------------------------------------------------- panel
+// Eliminates columns [k0, k0 + nbk) of every row of M (problem = blockIdx.x).
+// Thread t holds the nbk entries of rows t and t + blockDim.x (RPT = 2) or
+// of row t (RPT = 1) in registers.  Per column j: each warp finds its best
+// eligible row (largest |.|^2, lowest row on ties) and the winning lane
+// publishes that whole row in shared memory; after one block barrier every
+// warp reduces the per-warp candidates itself, reads the pivot row from
+// shared memory and eliminates (candidates double-buffered by step parity).
+// Outputs: the panel columns of M, rowpiv[r] = pivot column of the rows
+// pivoted here, pivslot[k0 + j] = pivot row of column k0 + j, and Bin =
+// M_old[P, slab] with the panel's own columns (and columns outside the slab)
+// zero: the right operand of the inner update.
+constexpr int GW_PANEL_THREADS = GW_PANEL_MAX / 2;
+
+__device__ __forceinline__ void gjw_load_row(const float2* M, int b, int row, int k0, int nbk,
+                                             bool ok, float2 (&x)[GW_NB]) {
+  const float4* src = reinterpret_cast<const float4*>(M + (size_t)(ok ? row : 0) * b + k0);
+#pragma unroll
+  for (int c = 0; c < GW_NB; c += 2) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ok && c < nbk) v = src[c >> 1];
+    x[c] = make_float2(v.x, v.y);
+    x[c + 1] = (c + 1 < nbk) ? make_float2(v.z, v.w) : make_float2(0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ void gjw_store_row(float2* M, int b, int row, int k0, int nbk,
+                                              const float2 (&x)[GW_NB]) {
+  float4* dst = reinterpret_cast<float4*>(M + (size_t)row * b + k0);
+#pragma unroll
+  for (int c = 0; c < GW_NB; c += 2)
+    if (c < nbk) {
+      if (c + 1 < nbk) dst[c >> 1] = make_float4(x[c].x, x[c].y, x[c + 1].x, x[c + 1].y);
+      else reinterpret_cast<float2*>(dst)[c] = x[c];
+    }
+}
+
+// pivot row after its step: every entry scaled by 1/pivot, the pivot column
+// holding 1/pivot itself
+__device__ __forceinline__ void gjw_scale_pivot(float2 (&x)[GW_NB], int J, float2 pinv,
+                                                const float2* prow) {
+#pragma unroll
+  for (int c = 0; c < GW_NB; ++c)
+    if (c != J) x[c] = cmul(prow[c], pinv);
+  x[J] = pinv;
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(GW_PANEL_THREADS, 1)
+gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Mall,
+                 int* __restrict__ rowpiv_all, int* __restrict__ pivslot_all,
+                 float2* __restrict__ Bin_all, int* __restrict__ flag) {
+  constexpr int NB = GW_NB;
+  constexpr int MAXW = GW_PANEL_THREADS / 32;
+  __shared__ float2 cand[2][MAXW][NB];
+  __shared__ float candv[2][MAXW];
+  __shared__ int candi[2][MAXW];
+  __shared__ int piv_sm[NB];
+  const int f = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int nt = blockDim.x, nw = nt >> 5;
+  const int r0 = t, r1 = t + nt;  // rows held (r1 only when RPT == 2)
+  const bool a0 = r0 < b, a1 = RPT == 2 && r1 < b;
+  float2* M = Mall + (size_t)f * b * b;
+  int* rowpiv = rowpiv_all + (size_t)f * b;
+
+  float2 x0[NB], x1[NB];
+  gjw_load_row(M, b, r0, k0, nbk, a0, x0);
+  if (RPT == 2) gjw_load_row(M, b, r1, k0, nbk, a1, x1);
+  bool e0 = a0 && rowpiv[r0] < 0;
+  bool e1 = a1 && rowpiv[r1] < 0;
+  int col0 = -1, col1 = -1;
+
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j >= nbk) break;
+    const int buf = j & 1;
+    // this thread's best eligible row, then the warp's
+    float bv = e0 ? x0[j].x * x0[j].x + x0[j].y * x0[j].y : -1.f;
+    int bi = a0 ? r0 : 0x7fffffff;
+    if (RPT == 2) {
+      const float v1 = e1 ? x1[j].x * x1[j].x + x1[j].y * x1[j].y : -1.f;
+      if (a1 && v1 > bv) { bv = v1; bi = r1; }
+    }
+    const int mine = bi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
+    }
+    if (bi == mine && bi != 0x7fffffff) {
+      if (RPT == 2 && bi == r1) {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) cand[buf][warp][c] = x1[c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) cand[buf][warp][c] = x0[c];
+      }
+      candv[buf][warp] = bv;
+      candi[buf][warp] = bi;
+    }
+    __syncthreads();
+    float pv = lane < nw ? candv[buf][lane] : -2.f;
+    int pi = lane < nw ? candi[buf][lane] : 0x7fffffff;
+    int pw = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float v2 = __shfl_xor_sync(0xffffffffu, pv, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, pi, o);
+      const int w2 = __shfl_xor_sync(0xffffffffu, pw, o);
+      if (v2 > pv || (v2 == pv && i2 < pi)) { pv = v2; pi = i2; pw = w2; }
+    }
+    if (t == 0) {
+      piv_sm[j] = pi;
+      if (!(pv > 0.f)) flag[f] = 1;
+    }
+    const float2* prow = cand[buf][pw];
+    float2 piv = prow[j];
+    if (piv.x * piv.x + piv.y * piv.y == 0.f) piv = make_float2(1e-18f, 0.f);
+    const float pd = piv.x * piv.x + piv.y * piv.y;
+    const float2 pinv = make_float2(piv.x / pd, -piv.y / pd);
+    // every held row: x -= (x_j / pivot) * pivot row, x_j <- -x_j / pivot;
+    // the pivot row itself is left alone here and scaled below
+    const bool p0 = r0 == pi, p1 = RPT == 2 && r1 == pi;
+    const float2 m0 = p0 ? make_float2(0.f, 0.f) : cmul(x0[j], pinv);
+    const float2 m1 = (RPT == 2 && !p1) ? cmul(x1[j], pinv) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c != j) {
+        const float2 p = prow[c];
+        x0[c].x = fmaf(-m0.x, p.x, fmaf(m0.y, p.y, x0[c].x));
+        x0[c].y = fmaf(-m0.x, p.y, fmaf(-m0.y, p.x, x0[c].y));
+        if (RPT == 2) {
+          x1[c].x = fmaf(-m1.x, p.x, fmaf(m1.y, p.y, x1[c].x));
+          x1[c].y = fmaf(-m1.x, p.y, fmaf(-m1.y, p.x, x1[c].y));
+        }
+      }
+    x0[j] = make_float2(-m0.x, -m0.y);
+    if (RPT == 2) x1[j] = make_float2(-m1.x, -m1.y);
+    if (p0) {
+      gjw_scale_pivot(x0, j, pinv, prow);
+      e0 = false;
+      col0 = j;
+    }
+    if (p1) {
+      gjw_scale_pivot(x1, j, pinv, prow);
+      e1 = false;
+      col1 = j;
+    }
+  }
+  // panel columns back in place; pivot bookkeeping
+  if (a0) {
+    gjw_store_row(M, b, r0, k0, nbk, x0);
+    if (col0 >= 0) rowpiv[r0] = k0 + col0;
+  }
+  if (a1) {
+    gjw_store_row(M, b, r1, k0, nbk, x1);
+    if (col1 >= 0) rowpiv[r1] = k0 + col1;
+  }
+  __syncthreads();
+  if (t < nbk) pivslot_all[(size_t)f * b + k0 + t] = piv_sm[t];
+  // Bin[f][c][m] = M_old[P_c][m] for m in the slab outside the panel, else 0
+  // (columns outside the slab are never read by the inner update)
+  float2* Bin = Bin_all + (size_t)f * NB * b;
+  const int wslab = c1 - c0;
+  for (int e = t; e < NB * wslab; e += nt) {
+    const int c = e / wslab, m = c0 + (e - c * wslab);
+    float2 v = make_float2(0.f, 0.f);
+    if (c < nbk && !(m >= k0 && m < k0 + nbk)) v = M[(size_t)piv_sm[c] * b + m];
+    Bin[(size_t)c * b + m] = v;
+  }
+}
+
+// Outer-update right operand: Bout[f][c][m] = M[P_{c0+c}][m] for m outside
+// [c0, c1) and c < c1 - c0; zero elsewhere (rows up to GW_W).
+__global__ void gjw_gather_kernel(int b, int c0, int c1, const float2* __restrict__ Mall,
+                                  const int* __restrict__ pivslot_all, float2* __restrict__ Bout) {
+  const int f = blockIdx.y;
+  const int c = blockIdx.x;  // 0 .. GW_W - 1
+  const float2* M = Mall + (size_t)f * b * b;
+  float2* dst = Bout + ((size_t)f * GW_W + c) * b;
+  const bool row_ok = c < c1 - c0;
+  const int p = row_ok ? pivslot_all[(size_t)f * b + c0 + c] : 0;
+  for (int m = threadIdx.x; m < b; m += blockDim.x) {
+    float2 v = make_float2(0.f, 0.f);
+    if (row_ok && (m < c0 || m >= c1)) v = M[(size_t)p * b + m];
+    dst[m] = v;
+  }
+}
+
+// --------------------------------------------------------------- tensor GEMM
+// C[f][rows][cols] += A'[f] B[f] for complex FP32 data:
+//   A'[r][c] = M[r][ka + c] - (rowpiv[r] == ka + c)   (b x Kc, from M by TMA)
+//   B        = Bbuf[f][0..Kc)[cols]                   (Kc x b rows by TMA)
+// Items (problem, 128-row tile, 64-column tile) over the column tiles of up
+// to two ranges; persistent CTAs take items round-robin.  Per item the
+// contraction runs in chunks of 16 complex columns of A (32 reals of K):
+//   control warp : TMA of the raw A chunk (128 x 32 floats) and B chunk (16 x
+//                  64 complex) into a 4-stage ring, and the MMAs of each
+//                  converted chunk into the item's TMEM accumulator (two, by
+//                  item parity);
+//   8 converter warps: split the raw chunk into operand pieces (K-major
+//                  core-matrix tiles; B expanded to the real 128 x 32 matrix
+//                  with rows (Re, -Im), (Im, Re) so one real GEMM gives the
+//                  complex product), double-buffered;
+//   8 epilogue warps: prefetch the item's rows of C, read the accumulator
+//                  (TMEM lane = row) and add it in place,
+// so the epilogue of item t overlaps the chunks of item t + 1.  Every wait is
+// bounded (tries polls); a timeout sets *err, every role winds down, and the
+// control thread drains its copies and MMAs before TMEM is freed.
+enum { SPLIT_TF32X3 = 0, SPLIT_BF16X3 = 1, SPLIT_BF16X6 = 2 };
+
+template <int SPLIT> struct SplitCfg;
+template <> struct SplitCfg<SPLIT_TF32X3> {
+  static constexpr int PIECES = 2, ESZ = 4, KSTEPS = 4, NPROD = 3;
+};
+template <> struct SplitCfg<SPLIT_BF16X3> {
+  static constexpr int PIECES = 2, ESZ = 2, KSTEPS = 2, NPROD = 3;
+};
+template <> struct SplitCfg<SPLIT_BF16X6> {
+  static constexpr int PIECES = 3, ESZ = 2, KSTEPS = 2, NPROD = 6;
+};
+// piece products (A piece, B piece) in the order they are accumulated: the
+// first three are hi.hi, hi.lo, lo.hi (x3 splits); BF16x6 adds the three
+// products of the next order, hi.lo2, lo.lo, lo2.hi
+__device__ __forceinline__ int prod_a(int pr) { return pr == 2 || pr == 4 ? 1 : pr == 5 ? 2 : 0; }
+__device__ __forceinline__ int prod_b(int pr) { return pr == 1 || pr == 4 ? 1 : pr == 3 ? 2 : 0; }
+
+constexpr int GG_RT = 128, GG_CT = 64, GG_KC = 16;  // rows, complex cols, complex K per chunk
+constexpr int GG_STAGES = 4;
+constexpr uint32_t GG_RAW_A = GG_RT * 2 * GG_KC * 4;  // 16 KB
+constexpr uint32_t GG_RAW_B = GG_KC * GG_CT * 8;      // 8 KB
+constexpr uint32_t GG_RAW_STAGE = GG_RAW_A + GG_RAW_B;
+constexpr int GG_EPI = 256, GG_CONV = 256;
+constexpr int GG_THREADS = GG_EPI + GG_CONV + 32;
+constexpr uint32_t GG_LBO = 128;
+
+template <int SPLIT>
+__host__ __device__ constexpr uint32_t gg_piece_bytes() {
+  return (uint32_t)GG_RT * 2 * GG_KC * SplitCfg<SPLIT>::ESZ;  // 128 rows x 32 reals
+}
+template <int SPLIT>
+__host__ __device__ constexpr uint32_t gg_sbo() {
+  return (uint32_t)(2 * GG_KC * SplitCfg<SPLIT>::ESZ / 16) * GG_LBO;  // core matrices per row group
+}
+template <int SPLIT>
+__host__ __device__ constexpr uint32_t gg_opbuf_bytes() {
+  return 2 * SplitCfg<SPLIT>::PIECES * gg_piece_bytes<SPLIT>();  // A pieces + B pieces
+}
+template <int SPLIT>
+__host__ __device__ constexpr size_t gg_smem_bytes() {
+  return 2 * (size_t)gg_opbuf_bytes<SPLIT>() + (size_t)GG_STAGES * GG_RAW_STAGE + 1024;
+}
+
+struct GemmArgs {
+  int b, F, ka, Kc;            // K range [ka, ka + Kc) of M's columns, Kc % 16 == 0
+  int x0, x1, y0, y1;          // column tiles [x0, x1) and [y0, y1) (64 complex each)
+  float2* M;
+  const int* rowpiv;           // [F][b]
+  int* err;
+  uint32_t tries;
+};
+
+__device__ __forceinline__ bool gg_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                        uint32_t tries) {
+  for (uint32_t t = 0; t < tries; ++t) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void gg_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// split of 4 consecutive reals into pieces, stored as one 16-byte (TF32) or
+// 8-byte (BF16) unit per piece
+template <int SPLIT>
+__device__ __forceinline__ void gg_store_split(float4 v, unsigned char* const* piece, uint32_t off) {
+  if constexpr (SPLIT == SPLIT_TF32X3) {
+    float4 h, l;
+    tc::split_tf32(v.x, h.x, l.x);
+    tc::split_tf32(v.y, h.y, l.y);
+    tc::split_tf32(v.z, h.z, l.z);
+    tc::split_tf32(v.w, h.w, l.w);
+    *reinterpret_cast<float4*>(piece[0] + off) = h;
+    *reinterpret_cast<float4*>(piece[1] + off) = l;
+  } else {
+    float r[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int p = 0; p < SplitCfg<SPLIT>::PIECES; ++p) {
+      __nv_bfloat162 lo2 = __floats2bfloat162_rn(r[0], r[1]);
+      __nv_bfloat162 hi2 = __floats2bfloat162_rn(r[2], r[3]);
+      uint2 u;
+      u.x = *reinterpret_cast<uint32_t*>(&lo2);
+      u.y = *reinterpret_cast<uint32_t*>(&hi2);
+      *reinterpret_cast<uint2*>(piece[p] + off) = u;
+      const float2 f0 = __bfloat1622float2(lo2), f1 = __bfloat1622float2(hi2);
+      r[0] -= f0.x;
+      r[1] -= f0.y;
+      r[2] -= f1.x;
+      r[3] -= f1.y;
+    }
+  }
+}
+
+// byte offset of real element (row, k) (k multiple of 4) in a K-major
+// core-matrix tile of 32 reals of K
+template <int SPLIT>
+__device__ __forceinline__ uint32_t gg_off(int row, int k) {
+  constexpr int ESZ = SplitCfg<SPLIT>::ESZ;
+  constexpr int EPC = 16 / ESZ;  // elements per 16-byte core row
+  return (uint32_t)(row >> 3) * gg_sbo<SPLIT>() + (uint32_t)(k / EPC) * GG_LBO +
+         (uint32_t)(row & 7) * 16 + (uint32_t)(k % EPC) * ESZ;
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(GG_THREADS, 1)
+gjw_gemm_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB,
+                GemmArgs g) {
+  using Cfg = SplitCfg<SPLIT>;
+  constexpr int PIECES = Cfg::PIECES;
+  constexpr uint32_t PB = gg_piece_bytes<SPLIT>();
+  constexpr uint32_t OPB = gg_opbuf_bytes<SPLIT>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t full_bar[GG_STAGES], opready[2], opfree[2], accfull[2], accempty[2], drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_sh;
+  volatile int* abort_flag = &abort_sh;
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  unsigned char* ops = base;                    // 2 operand buffers
+  unsigned char* raw = base + 2 * OPB;          // GG_STAGES raw stages
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool is_epi = tid < GG_EPI;
+  const bool is_conv = tid >= GG_EPI && tid < GG_EPI + GG_CONV;
+  const bool is_ctrl = tid == GG_EPI + GG_CONV;
+  const int b = g.b;
+  const int nrt = (b + GG_RT - 1) / GG_RT;
+  const int n1 = g.x1 - g.x0, nct = n1 + (g.y1 - g.y0);
+  const int nitems = g.F * nrt * nct;
+  const int nk = g.Kc / GG_KC;
+  const int my_items = nitems > (int)blockIdx.x
+                           ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                           : 0;
+  auto item = [&](int t, int& f, int& rt, int& ctile) {
+    const int it = (int)blockIdx.x + t * (int)gridDim.x;
+    const int ct = it % nct;
+    rt = (it / nct) % nrt;
+    f = it / (nct * nrt);
+    ctile = ct < n1 ? g.x0 + ct : g.y0 + (ct - n1);
+  };
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
+  if (tid == 0) {
+    for (int s = 0; s < GG_STAGES; ++s) tc::mbar_init(&full_bar[s], 1);
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&opready[q], GG_CONV);
+      tc::mbar_init(&opfree[q], 1);
+      tc::mbar_init(&accfull[q], 1);
+      tc::mbar_init(&accempty[q], GG_EPI);
+    }
+    tc::mbar_init(&drain, 1);
+    abort_sh = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (is_ctrl) {
+    // ---------------------------------------------------- control thread
+    const uint32_t idesc = SPLIT == SPLIT_TF32X3 ? tc::idesc_tf32(GG_RT, 2 * GG_CT)
+                                                 : tc::idesc_bf16(GG_RT, 2 * GG_CT);
+    int p_t = 0, p_kc = 0, issued = 0;
+    int pf = 0, prt = 0, pct = 0;
+    if (my_items > 0) item(0, pf, prt, pct);
+    auto issue_next = [&]() {
+      if (p_t >= my_items) return;
+      const int s = issued % GG_STAGES;
+      unsigned char* st = raw + s * GG_RAW_STAGE;
+      tc::mbar_expect_tx(&full_bar[s], GG_RAW_STAGE);
+      tc::tma_load_3d(st, &tmapA, 2 * (g.ka + p_kc * GG_KC), prt * GG_RT, pf, &full_bar[s]);
+      tc::tma_load_3d(st + GG_RAW_A, &tmapB, 2 * pct * GG_CT, p_kc * GG_KC, pf, &full_bar[s]);
+      ++issued;
+      if (++p_kc == nk) {
+        p_kc = 0;
+        if (++p_t < my_items) item(p_t, pf, prt, pct);
+      }
+    };
+    for (int q = 0; q < GG_STAGES; ++q) issue_next();
+    int gch = 0;
+    bool ok = true;
+    for (int t = 0; t < my_items && ok; ++t) {
+      const int a = t & 1;
+      if (t >= 2) ok = gg_wait(&accempty[a], (uint32_t)((t - 2) >> 1) & 1u, abort_flag, g.tries);
+      for (int kc = 0; kc < nk && ok; ++kc, ++gch) {
+        const int q = gch & 1;
+        ok = gg_wait(&opready[q], (uint32_t)(gch >> 1) & 1u, abort_flag, g.tries);
+        if (!ok) break;
+        issue_next();  // raw stage of chunk gch has been converted: refill it
+        tc::fence_after_sync();
+        const uint32_t acc = tmem + (uint32_t)a * (2 * GG_CT);
+        const uint32_t ob = tc::smem_u32(ops + q * OPB);
+#pragma unroll
+        for (int ks = 0; ks < Cfg::KSTEPS; ++ks) {
+#pragma unroll
+          for (int pr = 0; pr < Cfg::NPROD; ++pr) {
+            const int pa = prod_a(pr), pb = prod_b(pr);
+            const uint64_t da = tc::smem_desc(ob + pa * PB + ks * 2 * GG_LBO, GG_LBO, gg_sbo<SPLIT>());
+            const uint64_t db = tc::smem_desc(ob + (PIECES + pb) * PB + ks * 2 * GG_LBO, GG_LBO,
+                                              gg_sbo<SPLIT>());
+            const uint32_t accum = (kc > 0 || ks > 0 || pr > 0) ? 1u : 0u;
+            if (SPLIT == SPLIT_TF32X3) tc::mma_tf32(acc, da, db, idesc, accum);
+            else tc::mma_bf16(acc, da, db, idesc, accum);
+          }
+        }
+        tc::mma_commit(&opfree[q]);
+        if (kc == nk - 1) tc::mma_commit(&accfull[a]);
+      }
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      // copies still in flight: the last GG_STAGES issued chunks
+      for (int c = max(0, issued - GG_STAGES); c < issued; ++c)
+        tc::mbar_wait(&full_bar[c % GG_STAGES], (uint32_t)(c / GG_STAGES) & 1u, 1u << 22);
+    }
+    // every MMA this thread issued completes before TMEM is freed
+    tc::mma_commit(&drain);
+    tc::mbar_wait(&drain, 0, 1u << 22);
+  } else if (is_conv) {
+    // -------------------------------------------------------- converters
+    const int ct_id = tid - GG_EPI;
+    int gch = 0;
+    bool ok = true;
+    for (int t = 0; t < my_items && ok; ++t) {
+      int f, rt, ctile;
+      item(t, f, rt, ctile);
+      const int* rowpiv = g.rowpiv + (size_t)f * b;
+      for (int kc = 0; kc < nk; ++kc, ++gch) {
+        const int s = gch % GG_STAGES, q = gch & 1;
+        ok = gg_wait(&full_bar[s], (uint32_t)(gch / GG_STAGES) & 1u, abort_flag, g.tries);
+        if (ok && gch >= 2) ok = gg_wait(&opfree[q], (uint32_t)((gch - 2) >> 1) & 1u, abort_flag, g.tries);
+        if (!ok) break;
+        const float* RA = reinterpret_cast<const float*>(raw + s * GG_RAW_STAGE);
+        const float2* RB = reinterpret_cast<const float2*>(raw + s * GG_RAW_STAGE + GG_RAW_A);
+        unsigned char* ob = ops + q * OPB;
+        unsigned char* pa[3] = {ob, ob + PB, ob + 2 * PB};
+        unsigned char* pbp[3] = {ob + PIECES * PB, ob + (PIECES + 1) * PB, ob + (PIECES + 2) * PB};
+        const int kbase = g.ka + kc * GG_KC;  // first complex column of the chunk
+        // A: 128 rows x 8 units of 4 reals; rotated order for distinct banks
+        for (int it = ct_id; it < GG_RT * 8; it += GG_CONV) {
+          const int row = (it & 7) + 8 * (it >> 6);
+          const int p = (((it >> 3) & 7) + row) & 7;
+          float4 v = *reinterpret_cast<const float4*>(RA + row * 32 + 4 * p);
+          const int gr = rt * GG_RT + row;
+          if (gr < b) {
+            const int pc = rowpiv[gr] - (kbase + 2 * p);
+            if (pc == 0) v.x -= 1.f;
+            else if (pc == 1) v.z -= 1.f;
+          }
+          gg_store_split<SPLIT>(v, pa, gg_off<SPLIT>(row, 4 * p));
+        }
+        // B: 64 complex columns j x 8 pairs of K rows -> real rows 2j, 2j+1
+        for (int it = ct_id; it < GG_CT * 8; it += GG_CONV) {
+          const int j = it % GG_CT, pp = it / GG_CT;
+          const float2 t0 = RB[(2 * pp) * GG_CT + j], t1 = RB[(2 * pp + 1) * GG_CT + j];
+          gg_store_split<SPLIT>(make_float4(t0.x, -t0.y, t1.x, -t1.y), pbp, gg_off<SPLIT>(2 * j, 4 * pp));
+          gg_store_split<SPLIT>(make_float4(t0.y, t0.x, t1.y, t1.x), pbp, gg_off<SPLIT>(2 * j + 1, 4 * pp));
+        }
+        tc::fence_async_smem();
+        gg_arrive(&opready[q]);
+      }
+    }
+    if (!ok) *abort_flag = 1;
+  } else if (is_epi) {
+    // ---------------------------------------------------------- epilogue
+    const int lq = warp & 3, half = warp >> 2;
+    bool ok = true;
+    for (int t = 0; t < my_items && ok; ++t) {
+      int f, rt, ctile;
+      item(t, f, rt, ctile);
+      const int a = t & 1;
+      const int row = rt * GG_RT + lq * 32 + lane;
+      const int cb = ctile * GG_CT + half * 32;  // first complex column of this thread
+      float2* Mrow = g.M + ((size_t)f * b + (row < b ? row : 0)) * b;
+      const bool rv = row < b;
+      float4 cm[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int c = cb + 2 * u;
+        cm[u] = (rv && c < b) ? *reinterpret_cast<const float4*>(Mrow + c)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      ok = gg_wait(&accfull[a], (uint32_t)(t >> 1) & 1u, abort_flag, g.tries);
+      if (!ok) break;
+      tc::fence_after_sync();
+#pragma unroll
+      for (int grp = 0; grp < 4; ++grp) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)a * (2 * GG_CT) +
+                          (uint32_t)(half * 64 + grp * 16),
+                      v);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float4 m = cm[4 * grp + u];
+          m.x += v[4 * u];
+          m.y += v[4 * u + 1];
+          m.z += v[4 * u + 2];
+          m.w += v[4 * u + 3];
+          cm[4 * grp + u] = m;
+        }
+      }
+      tc::fence_before_sync();
+      gg_arrive(&accempty[a]);
+      if (rv) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int c = cb + 2 * u;
+          if (c < b) *reinterpret_cast<float4*>(Mrow + c) = cm[u];
+        }
+      }
+    }
+    if (!ok) *abort_flag = 1;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicExch(g.err, 1);
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// ---------------------------------------------------------------- finalize
+// G_i[j][p_m] = M[p_j][m] (S^{-1} from the implicitly pivoted work matrix),
+// X_i = G_i C_i with C_i = -L_{i,i+1} (at most 3q entries per row).
+__global__ void gjw_finalize_kernel(OpView op, int i, int RB, const float2* __restrict__ Mall,
+                                    const int* __restrict__ pivslot_all, float2* __restrict__ Gi,
+                                    size_t gstride, float2* __restrict__ Xi, size_t xstride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = op.b, q = op.q;
+  float2* Gs = reinterpret_cast<float2*>(smem_raw);        // [RB][b]
+  int* ps = reinterpret_cast<int*>(Gs + (size_t)RB * b);   // [b]
+  const int f = blockIdx.y;
+  const int r0 = blockIdx.x * RB;
+  const float2* M = Mall + (size_t)f * b * b;
+  for (int c = threadIdx.x; c < b; c += blockDim.x) ps[c] = pivslot_all[(size_t)f * b + c];
+  __syncthreads();
+  for (int e = threadIdx.x; e < RB * b; e += blockDim.x) {
+    const int rr = e / b, c = e - rr * b;
+    const int r = r0 + rr;
+    if (r < b) Gs[rr * b + ps[c]] = M[(size_t)ps[r] * b + c];
+  }
+  __syncthreads();
+  float2* G = Gi + (size_t)f * gstride;
+  for (int e = threadIdx.x; e < RB * b; e += blockDim.x) {
+    const int rr = e / b, c = e - rr * b;
+    const int r = r0 + rr;
+    if (r < b) G[(size_t)r * b + c] = Gs[rr * b + c];
+  }
+  if (Xi == nullptr) return;
+  float2* X = Xi + (size_t)f * xstride;
+  for (int e = threadIdx.x; e < RB * b; e += blockDim.x) {
+    const int rr = e / b, c = e - rr * b;
+    const int r = r0 + rr;
+    if (r >= b) continue;
+    const int iyc = c / q, cc = c - iyc * q;
+    float2 s = make_float2(0.f, 0.f);
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int iym = nbr_y(iyc, -dy, op.ny, op.periodic);
+      if (iym < 0) continue;
+      for (int cm = 0; cm < q; ++cm) {
+        const int m = iym * q + cm;
+        const float a = op.coef32[((size_t)i * b + m) * op.S + ((2) * 3 + (dy + 1)) * q + cc];
+        if (a != 0.f) s = crfma(a, Gs[rr * b + m], s);
+      }
+    }
+    X[(size_t)r * b + c] = make_float2(-s.x, -s.y);
+  }
+}
+
+__global__ void gjw_rowpiv_init_kernel(int* rowpiv, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) rowpiv[e] = -1;
+}
+
+template <int SPLIT>
+rr_status launch_gemm(rr_factors* fa, const CUtensorMap* ta, const CUtensorMap* tb, int ka, int Kc,
+                      int x0, int x1, int y0, int y1, cudaStream_t st) {
+  const OpDev& d = fa->op->d;
+  GemmArgs a;
+  a.b = d.b;
+  a.F = fa->F;
+  a.ka = ka;
+  a.Kc = Kc;
+  a.x0 = x0; a.x1 = x1; a.y0 = y0; a.y1 = y1;
+  a.M = reinterpret_cast<float2*>(fa->M);
+  a.rowpiv = fa->rowpiv;
+  a.err = fa->flag + fa->F;
+  a.tries = wait_tries();
+  const int nrt = (d.b + GG_RT - 1) / GG_RT;
+  const long items = (long)fa->F * nrt * ((x1 - x0) + (y1 - y0));
+  if (items <= 0) return RR_OK;
+  const int grid = (int)std::min<long>(items, num_sms(d.device));
+  static bool attr = false;
+  if (!attr) {
+    RR_CUDA(cudaFuncSetAttribute(gjw_gemm_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gg_smem_bytes<SPLIT>()));
+    attr = true;
+  }
+  prof_begin(PROF_UPDATE, st);
+  gjw_gemm_kernel<SPLIT><<<grid, GG_THREADS, gg_smem_bytes<SPLIT>(), st>>>(*ta, *tb, a);
+  prof_end(PROF_UPDATE, st);
+  RR_CUDA(cudaGetLastError());
+  return RR_OK;
+}
+
+template <int SPLIT>
+rr_status factor_wide_impl(rr_factors* fa) {
+  const OpDev& d = fa->op->d;
+  const OpView ov = view(d);
+  const int b = d.b, nx = d.nx, F = fa->F;
+  cudaStream_t st = fa->stream;
+  float2* M = reinterpret_cast<float2*>(fa->M);
+  float2* G = reinterpret_cast<float2*>(fa->G);
+  float2* X = reinterpret_cast<float2*>(fa->X);
+  const size_t bb = (size_t)b * b;
+  const CUtensorMap* tA = reinterpret_cast<const CUtensorMap*>(fa->wmap[0]);
+  const CUtensorMap* tBin = reinterpret_cast<const CUtensorMap*>(fa->wmap[1]);
+  const CUtensorMap* tBout = reinterpret_cast<const CUtensorMap*>(fa->wmap[2]);
+  int RB = 4;
+  while (RB > 1 && (size_t)RB * b * sizeof(float2) + b * sizeof(int) > 160 * 1024) RB >>= 1;
+  const size_t fsmem = (size_t)RB * b * sizeof(float2) + b * sizeof(int);
+  RR_CUDA(cudaFuncSetAttribute(gjw_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)fsmem));
+  const int nct_all = (b + GG_CT - 1) / GG_CT;
+  const int rpt = b > GW_PANEL_THREADS ? 2 : 1;
+  const int pthreads = ((b + rpt - 1) / rpt + 31) & ~31;
+  const int ncols = fa->factor_cols > 0 ? std::min(fa->factor_cols, nx) : nx;
+  for (int i = 0; i < ncols; ++i) {
+    prof_count(1);
+    gjw_rowpiv_init_kernel<<<(F * b + 255) / 256, 256, 0, st>>>(fa->rowpiv, F * b);
+    rr_status s = launch_schur_f32(fa, i, st);
+    if (s != RR_OK) return s;
+    for (int c0 = 0; c0 < b; c0 += GW_W) {
+      const int c1 = std::min(b, c0 + GW_W);
+      for (int k0 = c0; k0 < c1; k0 += GW_NB) {
+        const int nbk = std::min(GW_NB, c1 - k0);
+        prof_begin(PROF_PANEL, st);
+        if (rpt == 2)
+          gjw_panel_kernel<2><<<F, pthreads, 0, st>>>(b, k0, nbk, c0, c1, M, fa->rowpiv,
+                                                      fa->pivslot,
+                                                      reinterpret_cast<float2*>(fa->Bbuf), fa->flag);
+        else
+          gjw_panel_kernel<1><<<F, pthreads, 0, st>>>(b, k0, nbk, c0, c1, M, fa->rowpiv,
+                                                      fa->pivslot,
+                                                      reinterpret_cast<float2*>(fa->Bbuf), fa->flag);
+        prof_end(PROF_PANEL, st);
+        // the rest of the slab: column tiles of [c0, c1) (the panel's own
+        // columns get zero from Bin)
+        if (c1 - c0 > nbk) {
+          const int t0 = c0 / GG_CT, t1 = (c1 + GG_CT - 1) / GG_CT;
+          if ((s = launch_gemm<SPLIT>(fa, tA, tBin, k0, GW_NB, t0, t1, 0, 0, st)) != RR_OK) return s;
+        }
+      }
+      if (c1 < b || c0 > 0) {
+        prof_begin(PROF_ROWBLOCK, st);
+        gjw_gather_kernel<<<dim3(GW_W, F), 256, 0, st>>>(b, c0, c1, M, fa->pivslot,
+                                                        reinterpret_cast<float2*>(fa->Wbuf));
+        prof_end(PROF_ROWBLOCK, st);
+        const int s0 = c0 / GG_CT, s1 = (c1 + GG_CT - 1) / GG_CT;
+        if ((s = launch_gemm<SPLIT>(fa, tA, tBout, c0, GW_W, 0, s0, s1, nct_all, st)) != RR_OK)
+          return s;
+      }
+    }
+    float2* Xi = (i + 1 < nx) ? X : nullptr;
+    prof_begin(PROF_FINALIZE, st);
+    gjw_finalize_kernel<<<dim3((b + RB - 1) / RB, F), 256, fsmem, st>>>(
+        ov, i, RB, M, fa->pivslot, G + (size_t)i * bb, (size_t)nx * bb, Xi, bb);
+    prof_end(PROF_FINALIZE, st);
+    RR_CUDA(cudaGetLastError());
+  }
+  return RR_OK;
+}
+
+}  // namespace
+
+// The wide path needs FP32 factors, an even block of at most 768 rows (one
+// panel row per thread) and at least 64, and the TMA maps of M and of the
+// gathered pivot rows.
+bool factor_wide_ok(const rr_factors* fa) {
+  const int b = fa->op->d.b;
+  return fa->wide_ok && b >= 64 && b <= GW_PANEL_MAX && (b % 8) == 0 &&
+         (fa->prec == RR_FP32 || fa->prec == RR_FP32_BF16X3 || fa->prec == RR_FP32_BF16X6);
+}
+
+rr_status launch_factor_wide(rr_factors* fa) {
+  switch (fa->prec) {
+    case RR_FP32_BF16X3: return factor_wide_impl<SPLIT_BF16X3>(fa);
+    case RR_FP32_BF16X6: return factor_wide_impl<SPLIT_BF16X6>(fa);
+    default: return factor_wide_impl<SPLIT_TF32X3>(fa);
+  }
+}

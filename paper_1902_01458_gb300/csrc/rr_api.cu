@@ -426,7 +426,7 @@ static int encode_factor_maps(rr_factors* fa) {
 // tensor-core trailing update.  Needs b >= 128 and b % 8 == 0.
 static int encode_m_map(rr_factors* fa) {
   const OpDev& d = fa->op->d;
-  if (fa->prec != RR_FP32 || d.b < 128 || (d.b & 7)) return 0;
+  if (!tc_prec(fa->prec) || d.b < 128 || (d.b & 7)) return 0;
   cudaDriverEntryPointQueryResult q;
   void* fn = nullptr;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
@@ -444,6 +444,44 @@ static int encode_m_map(rr_factors* fa) {
                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 1 : 0;
+}
+
+// TMA maps of the wide factorisation (FP32 factors): chunks of 16 complex
+// columns x 128 rows of M (the left operand, read in place), and tiles of 16
+// rows x 64 complex of the gathered pivot rows Bbuf [F][32][b] (inner
+// update) and Wbuf [F][128][b] (outer update).
+static int encode_wide_maps(rr_factors* fa) {
+  const OpDev& d = fa->op->d;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr) {
+    cudaGetLastError();
+    return 0;
+  }
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const cuuint32_t es[3] = {1, 1, 1};
+  const cuuint64_t dm[3] = {(cuuint64_t)2 * d.b, (cuuint64_t)d.b, (cuuint64_t)fa->F};
+  const cuuint64_t sm[2] = {(cuuint64_t)2 * d.b * 4, (cuuint64_t)2 * d.b * d.b * 4};
+  const cuuint32_t boxA[3] = {32, 128, 1}, boxB[3] = {128, 16, 1};
+  const cuuint64_t di[3] = {(cuuint64_t)2 * d.b, 32, (cuuint64_t)fa->F};
+  const cuuint64_t si[2] = {(cuuint64_t)2 * d.b * 4, (cuuint64_t)2 * d.b * 32 * 4};
+  const cuuint64_t dw[3] = {(cuuint64_t)2 * d.b, 128, (cuuint64_t)fa->F};
+  const cuuint64_t sw[2] = {(cuuint64_t)2 * d.b * 4, (cuuint64_t)2 * d.b * 128 * 4};
+  CUresult r0 = encode(reinterpret_cast<CUtensorMap*>(fa->wmap[0]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                       3, fa->M, dm, sm, boxA, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r1 = encode(reinterpret_cast<CUtensorMap*>(fa->wmap[1]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                       3, fa->Bbuf, di, si, boxB, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = encode(reinterpret_cast<CUtensorMap*>(fa->wmap[2]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                       3, fa->Wbuf, dw, sw, boxB, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return (r0 == CUDA_SUCCESS && r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? 1 : 0;
 }
 
 // ----------------------------------------------------------------- operator
@@ -590,7 +628,8 @@ extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts
   if (!op || !shifts || !out) return arg_error("rr_factor: null argument");
   *out = nullptr;
   if (nshift < 1 || nshift > 65535) return arg_error("rr_factor: nshift must be in [1, 65535]");
-  if (prec != RR_FP64 && prec != RR_FP32 && prec != RR_FP32_SIMT)
+  if (prec != RR_FP64 && prec != RR_FP32 && prec != RR_FP32_SIMT && prec != RR_FP32_BF16X3 &&
+      prec != RR_FP32_BF16X6)
     return arg_error("rr_factor: unknown precision");
   for (int f = 0; f < 2 * nshift; ++f)
     if (!std::isfinite(shifts[f])) return arg_error("rr_factor: shifts must be finite");
@@ -614,11 +653,18 @@ extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts
   if ((s = dalloc(&fa->M, (size_t)nshift * bb * fa->csz)) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->Bbuf, (size_t)nshift * 32 * d.b * fa->csz)) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->Tbuf, (size_t)nshift * 128 * d.b * fa->csz)) != RR_OK) return fail(s);
-  if (prec == RR_FP32) {
+  if (tc_prec(prec)) {
     if ((s = dalloc(&fa->Pbuf, (size_t)4 * nshift * 64 * d.b * sizeof(float2))) != RR_OK)
       return fail(s);
     fa->tma_ok = encode_factor_maps(fa);
     fa->tma_m_ok = encode_m_map(fa);
+    if (d.b >= 64 && d.b <= 768 && d.b % 8 == 0) {
+      if ((s = dalloc(&fa->rowpiv, (size_t)nshift * d.b * sizeof(int))) != RR_OK) return fail(s);
+      if ((s = dalloc(&fa->pivslot, (size_t)nshift * d.b * sizeof(int))) != RR_OK) return fail(s);
+      if ((s = dalloc(&fa->Wbuf, (size_t)nshift * 128 * d.b * sizeof(float2))) != RR_OK)
+        return fail(s);
+      fa->wide_ok = encode_wide_maps(fa);
+    }
   }
   if ((s = dalloc(&fa->perm, (size_t)nshift * d.b * sizeof(int))) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->ipiv, (size_t)nshift * 32 * sizeof(int))) != RR_OK) return fail(s);
@@ -683,6 +729,9 @@ extern "C" rr_status rr_destroy_factors(rr_factors* fa) {
   cudaFree(fa->Pbuf);
   cudaFree(fa->perm);
   cudaFree(fa->ipiv);
+  cudaFree(fa->rowpiv);
+  cudaFree(fa->pivslot);
+  cudaFree(fa->Wbuf);
   cudaFree(fa->flag);
   cudaFree(fa->ws);
   if (fa->stream2) {
@@ -722,7 +771,7 @@ rr_status factors_view(rr_factors* parent, int f0, int nf, cudaStream_t st, rr_f
     return r;
   };
   if ((s = dalloc(&v->Tbuf, (size_t)nf * 128 * d.b * v->csz)) != RR_OK) return fail(s);
-  if (v->prec == RR_FP32) {
+  if (tc_prec(v->prec)) {
     if ((s = dalloc(&v->Pbuf, (size_t)4 * nf * 64 * d.b * sizeof(float2))) != RR_OK) return fail(s);
     v->tma_ok = encode_factor_maps(v);
   }

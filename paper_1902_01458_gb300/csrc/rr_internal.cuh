@@ -151,6 +151,12 @@ struct rr_factors {
   int tma_m_ok;      // 1 if the map of M was encoded
   int* perm;         // [F][b]
   int* ipiv;         // [F][32]
+  // wide (two-level, implicitly pivoted) factorisation of FP32 factors
+  int wide_ok;       // 1 if the buffers and TMA maps below exist
+  int* rowpiv;       // [F][b] pivot column of each row (-1: not yet pivoted)
+  int* pivslot;      // [F][b] pivot row of each column
+  void* Wbuf;        // [F][128][b] gathered pivot rows of a slab (outer update)
+  alignas(64) unsigned char wmap[3][128];  // TMA maps: A chunks of M, Bbuf rows, Wbuf rows
   int* flag;         // [F] singular-pivot flags
   double2* shifts;   // [F] device
   double2* shifts_h; // [F] host copy
@@ -179,6 +185,12 @@ struct rr_factors {
   int tune_update;
   int factor_cols;
 };
+
+// Precisions that store complex FP32 factors and run their products on the
+// tensor cores (TF32 or BF16 operand splits).
+inline bool tc_prec(int prec) {
+  return prec == RR_FP32 || prec == RR_FP32_BF16X3 || prec == RR_FP32_BF16X6;
+}
 
 enum { SCHED_EAGER = 0, SCHED_RECORD = 1, SCHED_REPLAY = 2 };
 enum { CHK_SOLVE = 0, CHK_CQR = 1 };
@@ -213,6 +225,11 @@ rr_status time_solve(rr_factors* fa, int k, float* ms);
 // factor.cu
 rr_status launch_factor(rr_factors* f);
 int factor_panel_width(int prec, int b);
+// M = D_i - A_i X_{i-1} for FP32 factors (the Schur update of column i)
+rr_status launch_schur_f32(rr_factors* f, int i, cudaStream_t st);
+// factor_w.cu: the wide FP32 factorisation (TF32 or BF16 operand splits)
+bool factor_wide_ok(const rr_factors* f);
+rr_status launch_factor_wide(rr_factors* f);
 
 // sweep.cu: x = A^{-1} b or A^{-H} b with the factors in precision T.
 // b and x are [F][N][k] in the factor precision; tmp same size (adjoint only).

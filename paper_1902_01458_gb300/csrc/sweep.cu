@@ -732,7 +732,7 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
   const size_t NK = (size_t)d.n * k;
   cudaStream_t st = fa->stream;
   if constexpr (std::is_same<T, float>::value) {
-    if (fa->prec == RR_FP32 && kp <= 32 && fa->tma_ok && (k % 2) == 0) {
+    if (tc_prec(fa->prec) && kp <= 32 && fa->tma_ok && (k % 2) == 0) {
       const int nrt = (b + TC_RT - 1) / TC_RT;
       const int nch = (b + TC2_KC - 1) / TC2_KC;
       const int nsm = num_sms(d.device);
@@ -775,7 +775,7 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
       RR_CUDA(cudaGetLastError());
       return RR_OK;
     }
-    if (fa->prec == RR_FP32 && kp <= 32) {
+    if (tc_prec(fa->prec) && kp <= 32) {
       const size_t smem = tc_smem_bytes(kp, TRANS) + 1024;
       static size_t tc_attr = 0;  // dynamic shared memory opted in so far
       if (smem > tc_attr) {
