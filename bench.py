@@ -35,14 +35,15 @@ import workloads as W  # noqa: E402
 
 HBM_PEAK_GBS = 6800.0       # profiling-recipe fallback (no MEASURED_PEAKS.json)
 BF16_PEAK_TFLOPS = 1900.0   # fallback burst figure
-# DRAM bytes (read + write) per launch of the timed kernel class from the ncu
-# captures summarised in profiles/ (batch 64, block 768; per-launch traffic
-# does not depend on nx).  Update: next-panel slice 25.2 MB (its writes stay
-# in L2), rest of the matrix 510.6 MB, averaged over the 11,776 + 12,288
-# launches of one factorisation.  Sweep: sweep_tc2_kernel, 315.0 MB read +
-# 26 MB written per column step.
-UPDATE_TRAFFIC = (11776 * 25.2e6 + 12288 * 510.6e6) / 24064
-SWEEP_TRAFFIC = 341.0e6
+# DRAM bytes (read + write) per launch of the timed kernel class from an ncu
+# capture of the current kernels (profiles/), or None when the kernel changed
+# since the counters were taken.
+UPDATE_TRAFFIC = None
+SWEEP_TRAFFIC = None
+PRECISIONS = ("fp32", "fp32_bf16x3", "fp32_bf16x6")
+# tensor-core MMAs per FP32-level product of each operand split
+SPLIT_MMAS = {"fp32": ("tf32", 3), "fp32_bf16x3": ("bf16", 3), "fp32_bf16x6": ("bf16", 6)}
+WIDE_SLAB, WIDE_PANEL = 128, 16
 
 
 def parse():
@@ -62,6 +63,9 @@ def parse():
     p.add_argument("--ny", type=int, default=256)
     p.add_argument("--k", type=int, default=32)
     p.add_argument("--roofline-class", default="update")
+    p.add_argument("--precision", default="fp32", choices=list(PRECISIONS),
+                   help="operand split of the FP32 factors' tensor-core products")
+    p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--workload", default="mixed", choices=["mixed", "batched"],
                    help="mixed: 512x256, k=32, 64 frequencies (default); "
                         "batched: the 128-problem uneven batch as one graph")
@@ -174,32 +178,31 @@ def batch_for(step, rank, world, F, omegas, seed0):
     return 1j * omegas[idx], [seed0 + i for i in idx], idx
 
 
-def update_flops_per_step(b, nx, NB, F):
-    tot = 0
-    for k0 in range(0, b, NB):
-        nbk = min(NB, b - k0)
-        tot += 8 * (b - nbk) ** 2 * nbk
-    return tot * nx * F
+def wide_gemm_work(b):
+    """Algorithmic work of the tensor-core updates of one Schur-block inverse
+    (block b) in the wide factorisation: per 128-column slab, the rank-16
+    updates of the slab's other columns and the rank-128 update of the
+    columns outside it.  Returns (real flops, HBM bytes) -- 8 flops per
+    complex multiply-add; bytes = one read and one write of every updated
+    complex FP32 entry of the work matrix (the operands stream from L2)."""
+    flops = byts = 0
+    for c0 in range(0, b, WIDE_SLAB):
+        w = min(WIDE_SLAB, b - c0)
+        for k0 in range(c0, c0 + w, WIDE_PANEL):
+            nbk = min(WIDE_PANEL, c0 + w - k0)
+            flops += 8 * b * (w - nbk) * nbk
+            byts += 16 * b * (w - nbk)
+        if b > w:
+            flops += 8 * b * (b - w) * w
+            byts += 16 * b * (b - w)
+    return flops, byts
 
 
-def update_bytes_per_step(b, nx, NB, F, csz=8):
-    """Algorithmic HBM bytes of all trailing updates of one factorisation:
-    per panel, one read and one write of every updated M[I,R] entry, one read
-    of the multipliers M[:,K] and of the saved pivot rows B = M[K,R]."""
-    tot = 0
-    for k0 in range(0, b, NB):
-        nbk = min(NB, b - k0)
-        w = b - nbk
-        tot += (w * w * 2 + b * nbk + nbk * w) * csz
-    return tot * nx * F
-
-
-def panel_width(prec_bytes, b):
-    cap = 227 * 1024 - 2048
-    for nb in (32, 16, 8):
-        if b * (nb + 1) * prec_bytes + 3 * nb * (nb + 1) * prec_bytes <= cap:
-            return nb
-    return 8
+def factor_flops(b):
+    """Gauss-Jordan inverse of one b x b complex block: b eliminations, each
+    updating b rows x (b - 1) other columns (8 real flops per complex
+    multiply-add)."""
+    return 8 * b * b * (b - 1)
 
 
 def metric_name(g, k):
@@ -316,8 +319,10 @@ def run_ours(args):
         U, sig, i2 = fa.modes(V)
         return sig, sh, i1, i2
 
+    # measured arithmetic peaks of this GPU (on-chip microbenchmarks)
+    unit_peaks = {u: _lib.rr_measure_peak(u, local) for u in ("tf32", "bf16", "fp64", "fp32")}
     shifts0, _, _ = batch_for(0, rank, world, F, wl.omegas, wl.seed0)
-    fa = rr.Factors(op, shifts0, "fp32", stream)
+    fa = rr.Factors(op, shifts0, args.precision, stream)
     info_last = None
     for s in range(args.warmup):
         step(fa, s)
@@ -358,25 +363,29 @@ def run_ours(args):
     # roofline of the timed kernel class
     b, nx = g.b, g.nx
     hbm, bf16, src = peaks()
+    unit, nmma = SPLIT_MMAS[args.precision]
+    tensor_peak = unit_peaks[unit] / nmma   # FP32-level flops of the split
     roof = None
     if cls_n > 0 and cls_ms > 0:
-        # achieved = algorithmic work of the timed region / event time of the
-        # class; per-launch figures are those totals over the launch count
         tot_s = cls_ms / 1e3
         if args.roofline_class == "update":
-            # rank-32 complex update: 8*32 flops per 16 bytes of M moved
-            # (16 flop/B), far below the TF32 ridge, so HBM bounds it
-            NB = panel_width(8, b)
-            work = update_bytes_per_step(b, nx, NB, F) * args.steps
-            flops = update_flops_per_step(b, nx, NB, F) * args.steps
-            ach = work / tot_s / 1e9
-            roof = {"kernel": "gj_update_tc_kernel (trailing rank-32 complex update, "
-                              "tcgen05 kind::tf32, 3xTF32)",
-                    "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": UPDATE_TRAFFIC, "peak_source": src,
-                    "algorithmic_per_launch": work / cls_n, "launches": cls_n,
+            # the factorisation's tensor-core updates (rank-16 slab updates
+            # and rank-128 updates): a complex contraction on the tensor
+            # pipe; achieved = algorithmic flops / the class's event time
+            gfl, gby = wide_gemm_work(b)
+            flops = gfl * nx * F * args.steps
+            byts = gby * nx * F * args.steps
+            ach = flops / tot_s / 1e12
+            roof = {"kernel": f"gjw_gemm_kernel (complex rank-16/128 updates of the Schur-block "
+                              f"inverse, tcgen05, {args.precision} operand split)",
+                    "bound": "tensor", "achieved": ach, "peak": tensor_peak, "unit": "TFLOP/s",
+                    "frac": ach / tensor_peak, "traffic": UPDATE_TRAFFIC,
+                    "peak_source": f"measured {unit} MMA peak {unit_peaks[unit]:.0f} TFLOP/s "
+                                   f"(rr_measure_peak) / {nmma} MMAs per FP32-level product",
+                    "algorithmic_per_launch": flops / cls_n, "launches": cls_n,
                     "avg_launch_us": tot_s / cls_n * 1e6,
-                    "algorithmic_tflops": flops / tot_s / 1e12}
+                    "hbm_achieved_gbs": byts / tot_s / 1e9, "hbm_frac": byts / tot_s / 1e9 / hbm,
+                    "hbm_peak_source": src}
         elif args.roofline_class == "sweep":
             work = F * (b * b * 8 + 3 * b * k * 8) * cls_n
             ach = work / tot_s / 1e9
@@ -385,38 +394,63 @@ def run_ours(args):
                     "frac": ach / hbm, "traffic": SWEEP_TRAFFIC, "peak_source": src,
                     "algorithmic_per_launch": work / cls_n, "launches": cls_n,
                     "avg_launch_us": tot_s / cls_n * 1e6}
+    # lower bound of one frequency: the factorisation's flops at the split's
+    # tensor peak plus the G_i streamed by every sweep of the solves actually
+    # run (each solve = forward + backward sweep, 1 + corrections solves)
+    corr = max(info_last[0]["refine_iters"], info_last[1]["refine_iters"])
+    n_solves = 3 * (1 + corr)
+    t_fac = factor_flops(b) * nx / (tensor_peak * 1e12)
+    t_sw = n_solves * 2 * nx * b * b * 8 / (hbm * 1e9)
+    per_omega = {"bound_ms": (t_fac + t_sw) * 1e3, "factor_ms": t_fac * 1e3,
+                 "sweeps_ms": t_sw * 1e3, "solves": n_solves,
+                 "measured_ms": elapsed_s * 1e3 / (F * args.steps) * world,
+                 "share_of_bound": (t_fac + t_sw) / (elapsed_s / (F * args.steps) * world)}
 
-    # FP64 path on a subset of the same frequencies, and sigma error vs it
+    # the FP64 GPU path on the same workload: warmed (its own factors object
+    # refactored for each step), allocation outside the timed region
     fp64 = None
     if not args.no_fp64 and rank == 0:
         F64 = args.fp64_batch
         fa.close()
         shifts, seeds, _ = batch_for(args.warmup, 0, 1, F64, wl.omegas, wl.seed0)
-        f32 = rr.Factors(op, shifts, "fp32", stream)
-        V, sh32, _ = f32.sketch(k, seeds, phi)
-        U, sig32, _ = f32.modes(V)
+        ref32 = rr.Factors(op, shifts, args.precision, stream)
+        V, sh32, _ = ref32.sketch(k, seeds, phi)
+        U, sig32, _ = ref32.modes(V)
         sig32 = sig32.cpu().numpy()
         sh32 = sh32.cpu().numpy()
-        f32.close()
+        ref32.close()
+        del V, U
+        f64 = rr.Factors(op, shifts, "fp64", stream)
+        V, sh64, _ = f64.sketch(k, seeds, phi)       # warm-up step
+        U, sig64, _ = f64.modes(V)
+        sig64 = sig64.cpu().numpy()
+        sh64 = sh64.cpu().numpy()
         del V, U
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        f64 = rr.Factors(op, shifts, "fp64", stream)
-        V, sh64, _ = f64.sketch(k, seeds, phi)
-        U, sig64, _ = f64.modes(V)
+        for s64 in range(args.fp64_steps):
+            sh_s, sd_s, _ = batch_for(args.warmup + 1 + s64, 0, 1, F64, wl.omegas, wl.seed0)
+            f64.refactor(sh_s)
+            V, _, _ = f64.sketch(k, sd_s, phi)
+            U, _, _ = f64.modes(V)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         t64 = e0.elapsed_time(e1) / 1e3
-        sig64 = sig64.cpu().numpy()
-        sh64 = sh64.cpu().numpy()
         f64.close()
         del V, U
-        fp64 = {"value": F64 / t64, "unit": "frequencies/s", "batch": F64,
+        v64 = F64 * args.fp64_steps / t64
+        ach64 = factor_flops(b) * nx * F64 * args.fp64_steps / t64 / 1e12
+        fp64 = {"value": v64, "unit": "frequencies/s", "batch": F64, "steps": args.fp64_steps,
+                "mixed_over_fp64": value / v64,
                 "sigma_rel_err_max": float(np.max(np.abs(sig32 - sig64) / sig64)),
                 "sigma_halko_rel_err_max": float(np.max(np.abs(sh32 - sh64) / sh64)),
-                "note": "one timed batch incl. factor allocation; first FP64 launch"}
+                "roofline": {"bound": "alu", "achieved": ach64, "peak": unit_peaks["fp64"],
+                             "unit": "TFLOP/s", "frac": ach64 / unit_peaks["fp64"],
+                             "note": "factorisation flops of the whole frequency over the "
+                                     "step time, against the measured FP64 FMA peak"},
+                "note": "warmed: one untimed batch, then refactor + Algorithm 1 per step"}
     else:
         fa.close()
 
@@ -436,7 +470,7 @@ def run_ours(args):
             op2 = rr.Operator(g, flow, device=local)
             h2d += 3 * g.npts * 8 + F * 16 + F * 8
             ph = op2.phi()
-            f2 = rr.Factors(op2, shifts, "fp32", stream)
+            f2 = rr.Factors(op2, shifts, args.precision, stream)
             V, sh, _ = f2.sketch(k, seeds, ph)
             U, sig, _ = f2.modes(V)
             Uh.copy_(U, non_blocking=True)
@@ -470,9 +504,11 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64+f64", "data": "synthetic",
             "config": workload_config(g, k, world), "frequencies_per_step_per_gpu": F,
-            "precision": "mixed: fp32 factors and tensor-core sweeps, fp64 refinement to "
-                         "1e-10, fp64 CholeskyQR2 + Jacobi SVD",
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
+            "precision": f"mixed: fp32 factors, tensor-core updates and sweeps in the "
+                         f"{args.precision} operand split, fp64 refinement to 1e-10, fp64 "
+                         f"CholeskyQR2 + Jacobi SVD",
+            "roofline": roof, "per_omega": per_omega, "measured_peaks": unit_peaks,
+            "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
             "clocks": clocks, "gpu_launches": launches,
             "refine": {"iters": max(info_last[0]["refine_iters"], info_last[1]["refine_iters"]),
                        "residual": max(info_last[0]["refine_residual"],

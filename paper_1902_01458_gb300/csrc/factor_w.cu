@@ -39,7 +39,8 @@ namespace {
 
 constexpr int GW_W = 128;   // slab width (rank of the outer update)
 constexpr int GW_NB = 16;   // panel width (rank of the inner update)
-constexpr int GW_PANEL_MAX = 768;  // rows a panel CTA holds (one per thread)
+constexpr int GW_PANEL_MAX = 768;  // rows a panel CTA holds (two per thread)
+constexpr int GW_BIN_ROWS = 32;    // row pitch per problem of the inner update's B buffer
 
 // ------------------------------------------------------------------- panel
 // Eliminates columns [k0, k0 + nbk) of every row of M (problem = blockIdx.x).
@@ -205,7 +206,7 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
   if (t < nbk) pivslot_all[(size_t)f * b + k0 + t] = piv_sm[t];
   // Bin[f][c][m] = M_old[P_c][m] for m in the slab outside the panel, else 0
   // (columns outside the slab are never read by the inner update)
-  float2* Bin = Bin_all + (size_t)f * NB * b;
+  float2* Bin = Bin_all + (size_t)f * GW_BIN_ROWS * b;
   const int wslab = c1 - c0;
   for (int e = t; e < NB * wslab; e += nt) {
     const int c = e / wslab, m = c0 + (e - c * wslab);
@@ -252,18 +253,13 @@ __global__ void gjw_gather_kernel(int b, int c0, int c1, const float2* __restric
 // so the epilogue of item t overlaps the chunks of item t + 1.  Every wait is
 // bounded (tries polls); a timeout sets *err, every role winds down, and the
 // control thread drains its copies and MMAs before TMEM is freed.
-enum { SPLIT_TF32X3 = 0, SPLIT_BF16X3 = 1, SPLIT_BF16X6 = 2 };
+using tc::SPLIT_BF16X3;
+using tc::SPLIT_BF16X6;
+using tc::SPLIT_TF32X3;
+template <int SPLIT> struct SplitCfg : tc::SplitCfg<SPLIT> {
+  static constexpr int KSTEPS = tc::ksteps32<SPLIT>();
+};
 
-template <int SPLIT> struct SplitCfg;
-template <> struct SplitCfg<SPLIT_TF32X3> {
-  static constexpr int PIECES = 2, ESZ = 4, KSTEPS = 4, NPROD = 3;
-};
-template <> struct SplitCfg<SPLIT_BF16X3> {
-  static constexpr int PIECES = 2, ESZ = 2, KSTEPS = 2, NPROD = 3;
-};
-template <> struct SplitCfg<SPLIT_BF16X6> {
-  static constexpr int PIECES = 3, ESZ = 2, KSTEPS = 2, NPROD = 6;
-};
 // piece products (A piece, B piece) in the order they are accumulated: the
 // first three are hi.hi, hi.lo, lo.hi (x3 splits); BF16x6 adds the three
 // products of the next order, hi.lo2, lo.lo, lo2.hi
@@ -285,7 +281,7 @@ __host__ __device__ constexpr uint32_t gg_piece_bytes() {
 }
 template <int SPLIT>
 __host__ __device__ constexpr uint32_t gg_sbo() {
-  return (uint32_t)(2 * GG_KC * SplitCfg<SPLIT>::ESZ / 16) * GG_LBO;  // core matrices per row group
+  return tc::sbo32<SPLIT>();  // 32 reals of K per row
 }
 template <int SPLIT>
 __host__ __device__ constexpr uint32_t gg_opbuf_bytes() {
@@ -317,47 +313,6 @@ __device__ __forceinline__ bool gg_wait(uint64_t* bar, uint32_t parity, volatile
 
 __device__ __forceinline__ void gg_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tc::smem_u32(bar)) : "memory");
-}
-
-// split of 4 consecutive reals into pieces, stored as one 16-byte (TF32) or
-// 8-byte (BF16) unit per piece
-template <int SPLIT>
-__device__ __forceinline__ void gg_store_split(float4 v, unsigned char* const* piece, uint32_t off) {
-  if constexpr (SPLIT == SPLIT_TF32X3) {
-    float4 h, l;
-    tc::split_tf32(v.x, h.x, l.x);
-    tc::split_tf32(v.y, h.y, l.y);
-    tc::split_tf32(v.z, h.z, l.z);
-    tc::split_tf32(v.w, h.w, l.w);
-    *reinterpret_cast<float4*>(piece[0] + off) = h;
-    *reinterpret_cast<float4*>(piece[1] + off) = l;
-  } else {
-    float r[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int p = 0; p < SplitCfg<SPLIT>::PIECES; ++p) {
-      __nv_bfloat162 lo2 = __floats2bfloat162_rn(r[0], r[1]);
-      __nv_bfloat162 hi2 = __floats2bfloat162_rn(r[2], r[3]);
-      uint2 u;
-      u.x = *reinterpret_cast<uint32_t*>(&lo2);
-      u.y = *reinterpret_cast<uint32_t*>(&hi2);
-      *reinterpret_cast<uint2*>(piece[p] + off) = u;
-      const float2 f0 = __bfloat1622float2(lo2), f1 = __bfloat1622float2(hi2);
-      r[0] -= f0.x;
-      r[1] -= f0.y;
-      r[2] -= f1.x;
-      r[3] -= f1.y;
-    }
-  }
-}
-
-// byte offset of real element (row, k) (k multiple of 4) in a K-major
-// core-matrix tile of 32 reals of K
-template <int SPLIT>
-__device__ __forceinline__ uint32_t gg_off(int row, int k) {
-  constexpr int ESZ = SplitCfg<SPLIT>::ESZ;
-  constexpr int EPC = 16 / ESZ;  // elements per 16-byte core row
-  return (uint32_t)(row >> 3) * gg_sbo<SPLIT>() + (uint32_t)(k / EPC) * GG_LBO +
-         (uint32_t)(row & 7) * 16 + (uint32_t)(k % EPC) * ESZ;
 }
 
 template <int SPLIT>
@@ -505,14 +460,14 @@ gjw_gemm_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant
             if (pc == 0) v.x -= 1.f;
             else if (pc == 1) v.z -= 1.f;
           }
-          gg_store_split<SPLIT>(v, pa, gg_off<SPLIT>(row, 4 * p));
+          tc::store_split<SPLIT>(v, pa, tc::kmajor_off32<SPLIT>(row, 4 * p));
         }
         // B: 64 complex columns j x 8 pairs of K rows -> real rows 2j, 2j+1
         for (int it = ct_id; it < GG_CT * 8; it += GG_CONV) {
           const int j = it % GG_CT, pp = it / GG_CT;
           const float2 t0 = RB[(2 * pp) * GG_CT + j], t1 = RB[(2 * pp + 1) * GG_CT + j];
-          gg_store_split<SPLIT>(make_float4(t0.x, -t0.y, t1.x, -t1.y), pbp, gg_off<SPLIT>(2 * j, 4 * pp));
-          gg_store_split<SPLIT>(make_float4(t0.y, t0.x, t1.y, t1.x), pbp, gg_off<SPLIT>(2 * j + 1, 4 * pp));
+          tc::store_split<SPLIT>(make_float4(t0.x, -t0.y, t1.x, -t1.y), pbp, tc::kmajor_off32<SPLIT>(2 * j, 4 * pp));
+          tc::store_split<SPLIT>(make_float4(t0.y, t0.x, t1.y, t1.x), pbp, tc::kmajor_off32<SPLIT>(2 * j + 1, 4 * pp));
         }
         tc::fence_async_smem();
         gg_arrive(&opready[q]);
@@ -686,35 +641,69 @@ rr_status factor_wide_impl(rr_factors* fa) {
     gjw_rowpiv_init_kernel<<<(F * b + 255) / 256, 256, 0, st>>>(fa->rowpiv, F * b);
     rr_status s = launch_schur_f32(fa, i, st);
     if (s != RR_OK) return s;
-    for (int c0 = 0; c0 < b; c0 += GW_W) {
+    // inner factorisation of one slab on stream sx: its panels and their
+    // rank-16 updates of the slab's other columns
+    auto inner = [&](int c0, cudaStream_t sx) -> rr_status {
       const int c1 = std::min(b, c0 + GW_W);
       for (int k0 = c0; k0 < c1; k0 += GW_NB) {
         const int nbk = std::min(GW_NB, c1 - k0);
-        prof_begin(PROF_PANEL, st);
+        prof_begin(PROF_PANEL, sx);
         if (rpt == 2)
-          gjw_panel_kernel<2><<<F, pthreads, 0, st>>>(b, k0, nbk, c0, c1, M, fa->rowpiv,
+          gjw_panel_kernel<2><<<F, pthreads, 0, sx>>>(b, k0, nbk, c0, c1, M, fa->rowpiv,
                                                       fa->pivslot,
                                                       reinterpret_cast<float2*>(fa->Bbuf), fa->flag);
         else
-          gjw_panel_kernel<1><<<F, pthreads, 0, st>>>(b, k0, nbk, c0, c1, M, fa->rowpiv,
+          gjw_panel_kernel<1><<<F, pthreads, 0, sx>>>(b, k0, nbk, c0, c1, M, fa->rowpiv,
                                                       fa->pivslot,
                                                       reinterpret_cast<float2*>(fa->Bbuf), fa->flag);
-        prof_end(PROF_PANEL, st);
-        // the rest of the slab: column tiles of [c0, c1) (the panel's own
-        // columns get zero from Bin)
+        prof_end(PROF_PANEL, sx);
+        // the rest of the slab: its column tiles (the panel's own columns get
+        // zero from Bin)
         if (c1 - c0 > nbk) {
           const int t0 = c0 / GG_CT, t1 = (c1 + GG_CT - 1) / GG_CT;
-          if ((s = launch_gemm<SPLIT>(fa, tA, tBin, k0, GW_NB, t0, t1, 0, 0, st)) != RR_OK) return s;
+          rr_status r = launch_gemm<SPLIT>(fa, tA, tBin, k0, GW_NB, t0, t1, 0, 0, sx);
+          if (r != RR_OK) return r;
         }
       }
-      if (c1 < b || c0 > 0) {
-        prof_begin(PROF_ROWBLOCK, st);
-        gjw_gather_kernel<<<dim3(GW_W, F), 256, 0, st>>>(b, c0, c1, M, fa->pivslot,
-                                                        reinterpret_cast<float2*>(fa->Wbuf));
-        prof_end(PROF_ROWBLOCK, st);
-        const int s0 = c0 / GG_CT, s1 = (c1 + GG_CT - 1) / GG_CT;
-        if ((s = launch_gemm<SPLIT>(fa, tA, tBout, c0, GW_W, 0, s0, s1, nct_all, st)) != RR_OK)
-          return s;
+      return RR_OK;
+    };
+    // Look-ahead: once the next slab's columns have received this slab's
+    // rank-128 update, the next slab's inner factorisation runs on the second
+    // (high-priority) stream while the rank-128 update of the remaining
+    // columns proceeds on the main stream; the two touch disjoint columns of
+    // M (rowpiv entries of the next slab's pivot rows change meanwhile, but
+    // only from "not pivoted" to a column outside this slab, which the main
+    // stream's update reads as "not a pivot of this slab" either way).  The
+    // next slab's pivot rows are gathered on the main stream after both.
+    cudaStream_t st2 = fa->stream2;
+    if ((s = inner(0, st)) != RR_OK) return s;
+    for (int c0 = 0; c0 < b; c0 += GW_W) {
+      const int c1 = std::min(b, c0 + GW_W);
+      if (c1 >= b && c0 == 0) break;  // one slab: no outer update
+      prof_begin(PROF_ROWBLOCK, st);
+      gjw_gather_kernel<<<dim3(GW_W, F), 256, 0, st>>>(b, c0, c1, M, fa->pivslot,
+                                                      reinterpret_cast<float2*>(fa->Wbuf));
+      prof_end(PROF_ROWBLOCK, st);
+      const int s0 = c0 / GG_CT, s1 = (c1 + GG_CT - 1) / GG_CT;
+      if (c1 < b) {
+        const int n1 = std::min(b, c1 + GW_W);
+        const int u1 = (n1 + GG_CT - 1) / GG_CT;  // tiles [s1, u1): the next slab
+        if ((s = launch_gemm<SPLIT>(fa, tA, tBout, c0, GW_W, s1, u1, 0, 0, st)) != RR_OK) return s;
+        if (st2 != nullptr) {
+          RR_CUDA(cudaEventRecord(fa->ev_next, st));
+          RR_CUDA(cudaStreamWaitEvent(st2, fa->ev_next, 0));
+          if ((s = inner(c1, st2)) != RR_OK) return s;
+          RR_CUDA(cudaEventRecord(fa->ev_panel, st2));
+          if ((s = launch_gemm<SPLIT>(fa, tA, tBout, c0, GW_W, 0, s0, u1, nct_all, st)) != RR_OK)
+            return s;
+          RR_CUDA(cudaStreamWaitEvent(st, fa->ev_panel, 0));
+        } else {
+          if ((s = launch_gemm<SPLIT>(fa, tA, tBout, c0, GW_W, 0, s0, u1, nct_all, st)) != RR_OK)
+            return s;
+          if ((s = inner(c1, st)) != RR_OK) return s;
+        }
+      } else {
+        if ((s = launch_gemm<SPLIT>(fa, tA, tBout, c0, GW_W, 0, s0, 0, 0, st)) != RR_OK) return s;
       }
     }
     float2* Xi = (i + 1 < nx) ? X : nullptr;

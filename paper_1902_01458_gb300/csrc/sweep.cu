@@ -457,10 +457,20 @@ constexpr uint32_t TC2_A_BYTES = TC_RT * 2 * TC2_KC * 4;  // 16 KB operand tile
 __host__ __device__ constexpr uint32_t tc2_stage_bytes(int kp) {
   return (TC2_TILE_BYTES + (uint32_t)TC2_KC * kp * 8 + 1023u) & ~1023u;
 }
-__host__ __device__ constexpr uint32_t tc2_b_bytes(int kp) { return (uint32_t)(2 * kp / 8) * TC2_SBO; }
+// one operand piece: A is 128 rows, B~ is 2 kp rows, of 32 reals of K
+template <int SPLIT>
+__host__ __device__ constexpr uint32_t tc2_a_piece() { return (TC_RT / 8) * tc::sbo32<SPLIT>(); }
+template <int SPLIT>
+__host__ __device__ constexpr uint32_t tc2_b_piece(int kp) {
+  return (uint32_t)(2 * kp / 8) * tc::sbo32<SPLIT>();
+}
+template <int SPLIT>
+__host__ __device__ constexpr uint32_t tc2_buf_bytes(int kp) {
+  return tc::SplitCfg<SPLIT>::PIECES * (tc2_a_piece<SPLIT>() + tc2_b_piece<SPLIT>(kp));
+}
+template <int SPLIT>
 __host__ __device__ constexpr size_t tc2_smem_bytes(int kp) {
-  return 2 * (2 * (size_t)TC2_A_BYTES + 2 * (size_t)tc2_b_bytes(kp)) +
-         (size_t)TC2_STAGES * tc2_stage_bytes(kp);
+  return 2 * (size_t)tc2_buf_bytes<SPLIT>(kp) + (size_t)TC2_STAGES * tc2_stage_bytes(kp);
 }
 
 __device__ __forceinline__ bool tc_poll(uint64_t* bar, uint32_t parity, uint32_t tries) {
@@ -470,7 +480,7 @@ __device__ __forceinline__ bool tc_poll(uint64_t* bar, uint32_t parity, uint32_t
 constexpr int TC2_CONV = 256;                 // converter threads (warps 0-7)
 constexpr int TC2_THREADS = TC2_CONV + 32;    // + control warp 8 (TMA producer, MMA issuer)
 
-template <bool TRANS>
+template <bool TRANS, int SPLIT>
 __global__ void __launch_bounds__(TC2_THREADS, 1)
 sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp, int blk,
                  int nx, int nrt, int KS, int cpp, const float2* rhs, size_t rstride,
@@ -479,9 +489,12 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
   __shared__ uint64_t full_bar[TC2_STAGES];
   __shared__ uint64_t mma_bar[2];
   __shared__ uint32_t tmem_base;
+  constexpr int PIECES = tc::SplitCfg<SPLIT>::PIECES;
+  constexpr bool X6 = SPLIT == tc::SPLIT_BF16X6;
   const int N = 2 * kp;
-  const uint32_t bt_bytes = tc2_b_bytes(kp);
-  const uint32_t buf_bytes = 2 * TC2_A_BYTES + 2 * bt_bytes;  // hi/lo A and B of one chunk
+  const uint32_t a_piece = tc2_a_piece<SPLIT>();
+  const uint32_t bt_bytes = tc2_b_piece<SPLIT>(kp);
+  const uint32_t buf_bytes = tc2_buf_bytes<SPLIT>(kp);  // pieces of A and B of one chunk
   unsigned char* ops = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   unsigned char* raw = ops + 2 * buf_bytes;  // TC2_STAGES stages, 1 KB aligned
@@ -493,11 +506,14 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
   const int my_items = nitems > (int)blockIdx.x
                            ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
                            : 0;
-  // Per K step two MMAs: A_hi x [B_hi | B_lo] (N = 2 * 2k, both hi products
-  // in one pass over A_hi) and A_lo x B_hi.  Two accumulator sets (even and
-  // odd K steps) keep consecutive MMAs independent; the epilogue adds the
-  // four partial sums.  Set layout: [hi.hi | hi.lo | lo.hi], 3N columns.
-  const uint32_t ncols = (N <= 32) ? 256u : 512u;
+  // x3 splits, per K step two MMAs: A_hi x [B_hi | B_lo] (N = 2 * 2k, both
+  // hi products in one pass over A_hi) and A_lo x B_hi.  Two accumulator sets
+  // (even and odd K steps) keep consecutive MMAs independent; the epilogue
+  // adds the six partial sums.  Set layout: [hi.hi | hi.lo | lo.hi], 3N
+  // columns.  BF16 x6, per K step three MMAs into one set of 6N columns:
+  // p0 x [q0 | q1 | q2], p1 x [q0 | q1], p2 x q0.
+  const uint32_t ncols = X6 ? (6 * N <= 128 ? 128u : 6 * N <= 256 ? 256u : 512u)
+                            : ((N <= 32) ? 256u : 512u);
   // work item t of this CTA -> (problem, row tile, contraction part)
   auto item = [&](int t, int& f, int& rt, int& ks) {
     const int it = (int)blockIdx.x + t * (int)gridDim.x;
@@ -552,19 +568,24 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
   };
   if (ctrl)
     for (int q = 0; q < TC2_STAGES; ++q) issue_next();
-  // operand descriptors of both buffers; a K step of 8 advances 256 bytes
-  uint64_t dA[2][2], dB[2][2];
+  // operand descriptors of both buffers (piece 0 of A and the pieces of A
+  // and of the stacked B~); a K step (32 bytes) advances 256 bytes
+  constexpr uint32_t SBO = tc::sbo32<SPLIT>();
+  uint64_t dA[2][3], dB[2];
   if (ctrl)
     for (int q = 0; q < 2; ++q) {
       const uint32_t a0 = tc::smem_u32(ops + q * buf_bytes);
-      dA[q][0] = tc::smem_desc(a0, TC_LBO, TC2_SBO);
-      dA[q][1] = tc::smem_desc(a0 + TC2_A_BYTES, TC_LBO, TC2_SBO);
-      dB[q][0] = tc::smem_desc(a0 + 2 * TC2_A_BYTES, TC_LBO, TC2_SBO);
-      dB[q][1] = tc::smem_desc(a0 + 2 * TC2_A_BYTES + bt_bytes, TC_LBO, TC2_SBO);
+      for (int pc = 0; pc < PIECES; ++pc) dA[q][pc] = tc::smem_desc(a0 + pc * a_piece, TC_LBO, SBO);
+      dB[q] = tc::smem_desc(a0 + PIECES * a_piece, TC_LBO, SBO);
     }
-
-  const uint32_t idesc_hi = tc::idesc_tf32(TC_RT, 2 * N);
-  const uint32_t idesc_lo = tc::idesc_tf32(TC_RT, N);
+  auto idesc = [](int n) {
+    return SPLIT == tc::SPLIT_TF32X3 ? tc::idesc_tf32(TC_RT, n) : tc::idesc_bf16(TC_RT, n);
+  };
+  const uint32_t id1 = idesc(N), id2 = idesc(2 * N), id3 = idesc(3 * N);
+  auto mma = [](uint32_t d, uint64_t a, uint64_t bb, uint32_t id, uint32_t acc) {
+    if (SPLIT == tc::SPLIT_TF32X3) tc::mma_tf32(d, a, bb, id, acc);
+    else tc::mma_bf16(d, a, bb, id, acc);
+  };
   int g = 0;  // chunks consumed so far (global over this CTA's items)
   bool failed = false;
   for (int t = 0; t < my_items && !failed; ++t) {
@@ -578,10 +599,10 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
         ok = tc_poll(&full_bar[s], (g / TC2_STAGES) & 1, tries);
         if (ok && g >= 2) ok = tc_poll(&mma_bar[q], ((g - 2) >> 1) & 1, tries);  // buffer q is free
         tc::fence_after_sync();
-        unsigned char* A_hi = ops + q * buf_bytes;
-        unsigned char* A_lo = A_hi + TC2_A_BYTES;
-        unsigned char* B_hi = A_lo + TC2_A_BYTES;
-        unsigned char* B_lo = B_hi + bt_bytes;
+        unsigned char* ob = ops + q * buf_bytes;
+        unsigned char* ap[3] = {ob, ob + a_piece, ob + 2 * a_piece};
+        unsigned char* bp[3] = {ob + PIECES * a_piece, ob + PIECES * a_piece + bt_bytes,
+                                ob + PIECES * a_piece + 2 * bt_bytes};
         const float* R = reinterpret_cast<const float*>(raw + s * stage_bytes);
         const float2* Rt = reinterpret_cast<const float2*>(raw + s * stage_bytes + TC2_TILE_BYTES);
         if (ok) {
@@ -597,15 +618,7 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
               const float2 c = *reinterpret_cast<const float2*>(R + (2 * p + 1) * 256 + 2 * r);
               gv = make_float4(a.x, -a.y, c.x, -c.y);
             }
-            float4 h, l;
-            tc::split_tf32(gv.x, h.x, l.x);
-            tc::split_tf32(gv.y, h.y, l.y);
-            tc::split_tf32(gv.z, h.z, l.z);
-            tc::split_tf32(gv.w, h.w, l.w);
-            const uint32_t off =
-                (uint32_t)(r >> 3) * TC2_SBO + (uint32_t)p * TC_LBO + (uint32_t)(r & 7) * 16;
-            *reinterpret_cast<float4*>(A_hi + off) = h;
-            *reinterpret_cast<float4*>(A_lo + off) = l;
+            tc::store_split<SPLIT>(gv, ap, tc::kmajor_off32<SPLIT>(r, 4 * p));
           }
           const int m0 = (ks * cpp + lc) * TC2_KC;
           for (int it = tid; it < kp * 8; it += TC2_CONV) {
@@ -613,22 +626,10 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
             const int ma = m0 + 2 * p, mb = ma + 1;
             const float2 t0 = (j < k && ma < b) ? Rt[(2 * p) * k + j] : make_float2(0.f, 0.f);
             const float2 t1 = (j < k && mb < b) ? Rt[(2 * p + 1) * k + j] : make_float2(0.f, 0.f);
-            float4 h0, l0;
-            tc::split_tf32(t0.x, h0.x, l0.x);
-            tc::split_tf32(-t0.y, h0.y, l0.y);
-            tc::split_tf32(t1.x, h0.z, l0.z);
-            tc::split_tf32(-t1.y, h0.w, l0.w);
-            const float4 h1 = make_float4(-h0.y, h0.x, -h0.w, h0.z);
-            const float4 l1 = make_float4(-l0.y, l0.x, -l0.w, l0.z);
-            const int n0 = 2 * j, n1 = 2 * j + 1;
-            const uint32_t o0 =
-                (uint32_t)(n0 >> 3) * TC2_SBO + (uint32_t)p * TC_LBO + (uint32_t)(n0 & 7) * 16;
-            const uint32_t o1 =
-                (uint32_t)(n1 >> 3) * TC2_SBO + (uint32_t)p * TC_LBO + (uint32_t)(n1 & 7) * 16;
-            *reinterpret_cast<float4*>(B_hi + o0) = h0;
-            *reinterpret_cast<float4*>(B_lo + o0) = l0;
-            *reinterpret_cast<float4*>(B_hi + o1) = h1;
-            *reinterpret_cast<float4*>(B_lo + o1) = l1;
+            tc::store_split<SPLIT>(make_float4(t0.x, -t0.y, t1.x, -t1.y), bp,
+                                   tc::kmajor_off32<SPLIT>(2 * j, 4 * p));
+            tc::store_split<SPLIT>(make_float4(t0.y, t0.x, t1.y, t1.x), bp,
+                                   tc::kmajor_off32<SPLIT>(2 * j + 1, 4 * p));
           }
         }
         tc::fence_async_smem();
@@ -639,12 +640,19 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
         tc::fence_after_sync();
         issue_next();  // stage s has been split: refill it
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
+        for (int kk = 0; kk < tc::ksteps32<SPLIT>(); ++kk) {
           const uint64_t koff = (uint64_t)(kk * 2 * TC_LBO >> 4);
-          const uint32_t set = tmem + (uint32_t)(kk & 1) * set_cols;
-          const uint32_t acc = (lc > 0 || kk > 1) ? 1u : 0u;
-          tc::mma_tf32(set, dA[q][0] + koff, dB[q][0] + koff, idesc_hi, acc);
-          tc::mma_tf32(set + 2 * N, dA[q][1] + koff, dB[q][0] + koff, idesc_lo, acc);
+          if (X6) {
+            const uint32_t acc = (lc > 0 || kk > 0) ? 1u : 0u;
+            mma(tmem, dA[q][0] + koff, dB[q] + koff, id3, acc);
+            mma(tmem + 3 * N, dA[q][1] + koff, dB[q] + koff, id2, acc);
+            mma(tmem + 5 * N, dA[q][2] + koff, dB[q] + koff, id1, acc);
+          } else {
+            const uint32_t set = tmem + (uint32_t)(kk & 1) * set_cols;
+            const uint32_t acc = (lc > 0 || kk > 1) ? 1u : 0u;
+            mma(set, dA[q][0] + koff, dB[q] + koff, id2, acc);
+            mma(set + 2 * N, dA[q][1] + koff, dB[q] + koff, id1, acc);
+          }
         }
         tc::mma_commit(&mma_bar[q]);
         ++committed;
@@ -664,8 +672,11 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
         const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 16);
         tc::tmem_ld16(ta, v);
 #pragma unroll
-        for (int a = 1; a < 6; ++a) {  // sets 0/1 x {hi.hi, hi.lo, lo.hi}
-          tc::tmem_ld16(ta + (uint32_t)(a / 3) * set_cols + (uint32_t)(a % 3) * N, w);
+        for (int a = 1; a < 6; ++a) {  // the six partial products
+          // x3: sets 0/1 x {hi.hi, hi.lo, lo.hi}; x6: p0.q0..2, p1.q0..1, p2.q0
+          const uint32_t col = X6 ? (uint32_t)(a * N)
+                                  : (uint32_t)(a / 3) * set_cols + (uint32_t)(a % 3) * N;
+          tc::tmem_ld16(ta + col, w);
 #pragma unroll
           for (int tt = 0; tt < 16; ++tt) v[tt] += w[tt];
         }
@@ -717,6 +728,25 @@ __global__ void sweep_combine_kernel(int F, int b, int k, int KS, size_t NK, int
   }
 }
 
+// One launch of the TMA-fed tensor-core sweep step in the factors' operand
+// split (partial products into Pbuf).
+template <bool TRANS, int SPLIT, typename C>
+rr_status launch_tc2(const CUtensorMap* tm, int grid_x, int b, int k, int kp, int blk, int nx,
+                     int nrt, int KS, int cpp, const C* rhs, size_t rstride, rr_factors* fa,
+                     cudaStream_t st) {
+  const size_t smem = tc2_smem_bytes<SPLIT>(kp) + 1024;
+  static size_t attr = 0;  // dynamic shared memory opted in so far
+  if (smem > attr) {
+    RR_CUDA(cudaFuncSetAttribute(sweep_tc2_kernel<TRANS, SPLIT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  sweep_tc2_kernel<TRANS, SPLIT><<<grid_x, TC2_THREADS, smem, st>>>(
+      *tm, b, k, kp, blk, nx, nrt, KS, cpp, reinterpret_cast<const float2*>(rhs), rstride,
+      reinterpret_cast<float2*>(fa->Pbuf), fa->F, fa->flag + fa->F, wait_tries(), take_stall());
+  return RR_OK;
+}
+
 template <typename T> struct SweepCfg;
 template <> struct SweepCfg<float> { static constexpr int KC = 32, ST = 3; };
 template <> struct SweepCfg<double> { static constexpr int KC = 16, ST = 2; };
@@ -754,18 +784,23 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
       const int cpp = (nch + KS - 1) / KS;
       const int nitems = nrt * F * KS;
       const int grid_x = std::min(nitems, nsm);
-      const size_t smem = tc2_smem_bytes(kp) + 1024;
-      static size_t tc2_attr = 0;
-      if (smem > tc2_attr) {
-        RR_CUDA(cudaFuncSetAttribute(sweep_tc2_kernel<TRANS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        tc2_attr = smem;
-      }
       const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(fa->tmap[TRANS ? 1 : 0]);
       prof_begin(PROF_SWEEP, st);
-      sweep_tc2_kernel<TRANS><<<grid_x, TC2_THREADS, smem, st>>>(
-          *tm, b, k, kp, blk, d.nx, nrt, KS, cpp, reinterpret_cast<const float2*>(rhs), rstride,
-          reinterpret_cast<float2*>(fa->Pbuf), F, fa->flag + F, wait_tries(), take_stall());
+      rr_status ls;
+      switch (fa->prec) {
+        case RR_FP32_BF16X3:
+          ls = launch_tc2<TRANS, tc::SPLIT_BF16X3>(tm, grid_x, b, k, kp, blk, d.nx, nrt, KS, cpp,
+                                                  rhs, rstride, fa, st);
+          break;
+        case RR_FP32_BF16X6:
+          ls = launch_tc2<TRANS, tc::SPLIT_BF16X6>(tm, grid_x, b, k, kp, blk, d.nx, nrt, KS, cpp,
+                                                  rhs, rstride, fa, st);
+          break;
+        default:
+          ls = launch_tc2<TRANS, tc::SPLIT_TF32X3>(tm, grid_x, b, k, kp, blk, d.nx, nrt, KS, cpp,
+                                                  rhs, rstride, fa, st);
+      }
+      if (ls != RR_OK) return ls;
       const size_t total = (size_t)F * b * k;
       const int cblocks = (int)std::min<size_t>((total + 255) / 256, 8192);
       sweep_combine_kernel<EPI><<<cblocks, 256, 0, st>>>(

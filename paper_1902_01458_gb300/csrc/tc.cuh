@@ -2,6 +2,7 @@
 // shared-memory matrix descriptors, mbarriers with bounded waits.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 namespace tc {
@@ -155,6 +156,81 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(x));
   hi = __uint_as_float(h);
   lo = x - hi;
+}
+
+// ---- FP32 operands as sums of lower-precision pieces ----------------------
+// An FP32 operand x is split into pieces whose sum is x to the split's
+// accuracy, and a product of two operands is the sum of the piece products
+// that matter at FP32 level:
+//   TF32x3: x = hi + lo (hi = TF32 rounding, lo the exact remainder, read by
+//           the tensor core as TF32): hi.hi + hi.lo + lo.hi;
+//   BF16x3: x = p0 + p1 (BF16 roundings of x and of the remainder; about 16
+//           bits): p0.q0 + p0.q1 + p1.q0;
+//   BF16x6: x = p0 + p1 + p2 (about 24 bits): the six products of order at
+//           most 2, p0.q0 + p0.q1 + p1.q0 + p0.q2 + p1.q1 + p2.q0.
+enum { SPLIT_TF32X3 = 0, SPLIT_BF16X3 = 1, SPLIT_BF16X6 = 2 };
+
+template <int SPLIT> struct SplitCfg;
+template <> struct SplitCfg<SPLIT_TF32X3> {
+  static constexpr int PIECES = 2, ESZ = 4, NPROD = 3;
+};
+template <> struct SplitCfg<SPLIT_BF16X3> {
+  static constexpr int PIECES = 2, ESZ = 2, NPROD = 3;
+};
+template <> struct SplitCfg<SPLIT_BF16X6> {
+  static constexpr int PIECES = 3, ESZ = 2, NPROD = 6;
+};
+
+// K-step of one MMA: 32 bytes (8 TF32 or 16 BF16 elements); a chunk of 32
+// reals of K is 4 (TF32) or 2 (BF16) steps
+template <int SPLIT>
+__host__ __device__ constexpr int ksteps32() { return SplitCfg<SPLIT>::ESZ == 4 ? 4 : 2; }
+
+// Byte offset of real element (row, k), k a multiple of 4, in a K-major
+// core-matrix tile holding 32 reals of K per row (8-row x 16-byte core
+// matrices, LBO = 128 bytes along K, SBO = 8 core matrices (TF32) or 4
+// (BF16) between 8-row groups).
+template <int SPLIT>
+__host__ __device__ constexpr uint32_t sbo32() {
+  return (uint32_t)(32 * SplitCfg<SPLIT>::ESZ / 16) * 128u;
+}
+template <int SPLIT>
+__device__ __forceinline__ uint32_t kmajor_off32(int row, int k) {
+  constexpr int ESZ = SplitCfg<SPLIT>::ESZ;
+  constexpr int EPC = 16 / ESZ;  // elements per 16-byte core row
+  return (uint32_t)(row >> 3) * sbo32<SPLIT>() + (uint32_t)(k / EPC) * 128u +
+         (uint32_t)(row & 7) * 16u + (uint32_t)(k % EPC) * ESZ;
+}
+
+// Split 4 consecutive reals of one row and store them as one 16-byte
+// (TF32) or 8-byte (BF16) unit per piece at byte offset off of each piece.
+template <int SPLIT>
+__device__ __forceinline__ void store_split(float4 v, unsigned char* const* piece, uint32_t off) {
+  if constexpr (SPLIT == SPLIT_TF32X3) {
+    float4 h, l;
+    split_tf32(v.x, h.x, l.x);
+    split_tf32(v.y, h.y, l.y);
+    split_tf32(v.z, h.z, l.z);
+    split_tf32(v.w, h.w, l.w);
+    *reinterpret_cast<float4*>(piece[0] + off) = h;
+    *reinterpret_cast<float4*>(piece[1] + off) = l;
+  } else {
+    float r[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int p = 0; p < SplitCfg<SPLIT>::PIECES; ++p) {
+      __nv_bfloat162 lo2 = __floats2bfloat162_rn(r[0], r[1]);
+      __nv_bfloat162 hi2 = __floats2bfloat162_rn(r[2], r[3]);
+      uint2 u;
+      u.x = *reinterpret_cast<uint32_t*>(&lo2);
+      u.y = *reinterpret_cast<uint32_t*>(&hi2);
+      *reinterpret_cast<uint2*>(piece[p] + off) = u;
+      const float2 f0 = __bfloat1622float2(lo2), f1 = __bfloat1622float2(hi2);
+      r[0] -= f0.x;
+      r[1] -= f0.y;
+      r[2] -= f1.x;
+      r[3] -= f1.y;
+    }
+  }
 }
 
 }  // namespace tc
