@@ -512,7 +512,11 @@ def run_ours(args):
             "clocks": clocks, "gpu_launches": launches,
             "refine": {"iters": max(info_last[0]["refine_iters"], info_last[1]["refine_iters"]),
                        "residual": max(info_last[0]["refine_residual"],
-                                       info_last[1]["refine_residual"])},
+                                       info_last[1]["refine_residual"]),
+                       "first_residual": max(info_last[0]["first_residual"],
+                                             info_last[1]["first_residual"]),
+                       "stagnated": bool(info_last[0]["refine_stagnated"]
+                                         or info_last[1]["refine_stagnated"])},
             "wall_s_timed": wall,
         }
         if breakdown:

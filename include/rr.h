@@ -125,6 +125,9 @@ typedef struct {
   int refine_stagnated;   /* 1 if refinement stopped at the FP64 residual
                              floor (a correction no longer halved the
                              residual) above refine_tol                    */
+  double first_residual;  /* largest ||b - A x|| / ||b|| per column after
+                             the first, uncorrected solve (the accuracy of
+                             the factors themselves)                       */
 } rr_info;
 
 const char* rr_last_error(void);

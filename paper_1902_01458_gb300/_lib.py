@@ -57,7 +57,7 @@ OMEGA_KINDS = {"gaussian": 0, "rademacher": 1, "sparse_rademacher": 2, "orthonor
 class rr_info(ctypes.Structure):
     _fields_ = [("refine_iters", ctypes.c_int), ("refine_residual", ctypes.c_double),
                 ("cqr_cond", ctypes.c_double), ("cqr_shifted", ctypes.c_int),
-                ("refine_stagnated", ctypes.c_int)]
+                ("refine_stagnated", ctypes.c_int), ("first_residual", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

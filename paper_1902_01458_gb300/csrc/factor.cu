@@ -31,53 +31,72 @@ constexpr int PANEL_THREADS = 512;
 __device__ __forceinline__ int slotx(int dx, int dy) { return (dx + 1) * 3 + (dy + 1); }
 
 // M = D_i (+ L_{i,i-1} X_{i-1} for i > 0), i.e. S_i = D_i - A_i X_{i-1}.  One
-// CTA per (SCHUR_ROWS rows, problem): a row's stencil coefficients are read
-// once (uniform loads) and its columns are spread over the threads.
-constexpr int SCHUR_ROWS = 4, SCHUR_THREADS = 256;
+// CTA per (SCHUR_Y grid points in y = SCHUR_Y * q rows, column tile, problem):
+// the rows of X_{i-1} its rows couple to (the y neighbours, SCHUR_Y + 2
+// points) are staged once in shared memory, so every X row is read from
+// memory about once instead of once per coupled row; a row's stencil
+// coefficients are uniform across the CTA (broadcast loads).
+constexpr int SCHUR_Y = 8, SCHUR_THREADS = 256;
+template <typename T> struct SchurCfg { static constexpr int CB = sizeof(T) == 4 ? 256 : 128; };
+template <typename T>
+__host__ __device__ constexpr size_t schur_smem(int q) {
+  return (size_t)(SCHUR_Y + 2) * q * SchurCfg<T>::CB * sizeof(C_t<T>);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(SCHUR_THREADS)
 schur_kernel(OpView op, const double2* __restrict__ shifts, int i,
              const C_t<T>* __restrict__ Xprev, size_t xstride, C_t<T>* __restrict__ M) {
   using C = C_t<T>;
-  const int b = op.b, q = op.q;
-  const int f = blockIdx.y;
+  constexpr int CB = SchurCfg<T>::CB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Xs = reinterpret_cast<C*>(smem_raw);  // [(SCHUR_Y + 2) * q][CB]
+  const int b = op.b, q = op.q, ny = op.ny;
+  const int f = blockIdx.z;
+  const int y0 = blockIdx.x * SCHUR_Y;
+  const int c0 = blockIdx.y * CB;
   const C sh = mk((T)shifts[f].x, (T)shifts[f].y);
   const C* Xp = Xprev ? Xprev + (size_t)f * xstride : nullptr;
   C* Mf = M + (size_t)f * b * b;
-  for (int rr = 0; rr < SCHUR_ROWS; ++rr) {
-    const int r = blockIdx.x * SCHUR_ROWS + rr;
-    if (r >= b) break;
-    const int iy = r / q;
-    const size_t cf = ((size_t)i * b + r) * op.S;
-    // D_i entries (x-offset 0) and A_i entries (x-offset -1) of row r: three
-    // neighbours in y times q <= 3 components
-    // (entry t = (dy + 1) * q + cp; unrolled so the arrays stay in registers)
-    int cols[9];
-    T dval[9], aval[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      cols[t] = -1;
-      dval[t] = aval[t] = (T)0;
-      if (t < 3 * q) {
-        const int dy = t / q - 1, cp = t - (t / q) * q;
-        const int jy = nbr_y(iy, dy, op.ny, op.periodic);
-        if (jy >= 0) {
-          cols[t] = jy * q + cp;
-          dval[t] = coefv<T>(op, cf + slotx(0, dy) * q + cp);
-          aval[t] = coefv<T>(op, cf + slotx(-1, dy) * q + cp);
-        }
-      }
+  const int ny_blk = min(SCHUR_Y, ny - y0);
+  // stage X rows of y points y0 - 1 .. y0 + ny_blk (slot k <-> point y0 - 1 + k)
+  if (Xp) {
+    const int nslots = (ny_blk + 2) * q;
+    for (int e = threadIdx.x; e < nslots * CB; e += SCHUR_THREADS) {
+      const int sl = e / CB, cc = e - sl * CB;
+      const int pt = sl / q, comp = sl - pt * q;
+      // point y0 - 1 + pt, wrapped when y is periodic (outside the grid
+      // otherwise: never read, its coupling coefficient is absent)
+      const int yy = op.periodic ? (y0 - 1 + pt + ny) % ny : y0 - 1 + pt;
+      const int c = c0 + cc;
+      C v = czero<C>();
+      if (c < b && yy >= 0 && yy < ny) v = Xp[(size_t)(yy * q + comp) * b + c];
+      Xs[sl * CB + cc] = v;
     }
-    for (int c = threadIdx.x; c < b; c += SCHUR_THREADS) {
+    __syncthreads();
+  }
+  const int c = c0 + threadIdx.x;
+  if (c >= b) return;
+  for (int ly = 0; ly < ny_blk; ++ly) {
+    const int iy = y0 + ly;
+    for (int comp = 0; comp < q; ++comp) {
+      const int r = iy * q + comp;
+      const size_t cf = ((size_t)i * b + r) * op.S;
       C val = (r == c) ? sh : czero<C>();
 #pragma unroll
-      for (int t = 0; t < 9; ++t)
-        if (cols[t] == c) val.x -= dval[t];
-      if (Xp) {
-#pragma unroll
-        for (int t = 0; t < 9; ++t)
-          if (cols[t] >= 0 && aval[t] != (T)0)
-            val = crfma(aval[t], Xp[(size_t)cols[t] * b + c], val);
+      for (int t = 0; t < 9; ++t) {
+        if (t >= 3 * q) break;
+        const int dy = t / q - 1, cp = t - (t / q) * q;
+        const int jy = nbr_y(iy, dy, ny, op.periodic);
+        if (jy < 0) continue;
+        const T dv = coefv<T>(op, cf + slotx(0, dy) * q + cp);
+        if (jy * q + cp == c) val.x -= dv;
+        if (Xp) {
+          const T av = coefv<T>(op, cf + slotx(-1, dy) * q + cp);
+          // slot of point iy + dy: ly + 1 + dy (periodic wrap stays in the
+          // staged range because the staged points are y0 - 1 .. y0 + ny_blk)
+          if (av != (T)0) val = crfma(av, Xs[((ly + 1 + dy) * q + cp) * CB + threadIdx.x], val);
+        }
       }
       Mf[(size_t)r * b + c] = val;
     }
@@ -794,6 +813,21 @@ int panel_nb(int b) {
   return 8;
 }
 
+template <typename T>
+void launch_schur(const OpView& ov, const double2* shifts, int i, const C_t<T>* Xprev,
+                  size_t xstride, C_t<T>* M, int F, cudaStream_t st) {
+  constexpr int CB = SchurCfg<T>::CB;
+  const size_t smem = Xprev ? schur_smem<T>(ov.q) : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(schur_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)schur_smem<T>(3));
+    attr = true;
+  }
+  dim3 gs((ov.ny + SCHUR_Y - 1) / SCHUR_Y, (ov.b + CB - 1) / CB, F);
+  schur_kernel<T><<<gs, SCHUR_THREADS, smem, st>>>(ov, shifts, i, Xprev, xstride, M);
+}
+
 template <typename T, int NB>
 rr_status factor_impl(rr_factors* fa) {
   using C = C_t<T>;
@@ -868,10 +902,9 @@ rr_status factor_impl(rr_factors* fa) {
   for (int i = 0; i < ncols; ++i) {
     iota_kernel<<<(b * F + 255) / 256, 256, 0, st>>>(fa->perm, b, F);
     prof_count(1);
-    dim3 gs((b + SCHUR_ROWS - 1) / SCHUR_ROWS, F);
     const C* Xprev = (i > 0) ? X : nullptr;
     prof_begin(PROF_SCHUR, st);
-    schur_kernel<T><<<gs, SCHUR_THREADS, 0, st>>>(ov, fa->shifts, i, Xprev, xstride, M);
+    launch_schur<T>(ov, fa->shifts, i, Xprev, xstride, M, F, st);
     prof_end(PROF_SCHUR, st);
     panel(0, st);
     for (int p = 0; p < P; ++p) {
@@ -924,10 +957,9 @@ rr_status launch_schur_f32(rr_factors* fa, int i, cudaStream_t st) {
   const OpDev& d = fa->op->d;
   const int b = d.b;
   float2* X = reinterpret_cast<float2*>(fa->X);
-  dim3 gs((b + SCHUR_ROWS - 1) / SCHUR_ROWS, fa->F);
   prof_begin(PROF_SCHUR, st);
-  schur_kernel<float><<<gs, SCHUR_THREADS, 0, st>>>(view(d), fa->shifts, i, i > 0 ? X : nullptr,
-                                                   (size_t)b * b, reinterpret_cast<float2*>(fa->M));
+  launch_schur<float>(view(d), fa->shifts, i, i > 0 ? X : nullptr, (size_t)b * b,
+                      reinterpret_cast<float2*>(fa->M), fa->F, st);
   prof_end(PROF_SCHUR, st);
   RR_CUDA(cudaGetLastError());
   return RR_OK;

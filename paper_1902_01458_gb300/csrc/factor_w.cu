@@ -16,13 +16,17 @@
 //     panel  : one CTA per problem holds the tall panel M[:, K] in registers
 //              (one row per thread) and applies the 32 eliminations to it,
 //              recording the pivot rows P;
-//     update : M[:, slab \ K] += (M[:, K] - I[:, P]) * M_old[P, slab \ K]
-//              (the transformations of K applied to the rest of the slab);
+//     update : the transformations of K applied to the rest of the slab,
+//              M[r, slab \ K] += M[r, K] * M_old[P, slab \ K] for rows r not in
+//              P and M[P, slab \ K] = M[P, K] * M_old[P, slab \ K] (the
+//              pivot rows take T^{-1} B itself: adding (T^{-1} - I) B to B
+//              would cancel when T^{-1} is small);
 //   outer:
 //     gather : B = M[P_slab, outside the slab] (the pivot rows, saved before
 //              they change);
-//     update : M[:, outside] += (M[:, slab] - I[:, P_slab]) * B, the composed
-//              transformation of the slab's 128 eliminations applied at once.
+//     update : the composed transformation of the slab's 128 eliminations
+//              applied at once, M[r, outside] += M[r, slab] * B (r not in
+//              P_slab), M[P_slab, outside] = M[P_slab, slab] * B.
 // Both updates are one tensor-core kernel (gjw_gemm_kernel): a complex GEMM
 // C += A B with A read from M (minus the identity at the pivot rows) and B
 // from the gathered rows, as a real GEMM on tcgen05 with the operands split
@@ -234,9 +238,11 @@ __global__ void gjw_gather_kernel(int b, int c0, int c1, const float2* __restric
 }
 
 // --------------------------------------------------------------- tensor GEMM
-// C[f][rows][cols] += A'[f] B[f] for complex FP32 data:
-//   A'[r][c] = M[r][ka + c] - (rowpiv[r] == ka + c)   (b x Kc, from M by TMA)
-//   B        = Bbuf[f][0..Kc)[cols]                   (Kc x b rows by TMA)
+// C[f][rows][cols] (+)= A[f] B[f] for complex FP32 data:
+//   A = M[f][:, ka .. ka + Kc)          (b x Kc, from M by TMA)
+//   B = Bbuf[f][0..Kc)[cols]            (Kc x b rows by TMA)
+// rows pivoted in [ka, ka + Kc) are overwritten with the product, the other
+// rows accumulate it, and the columns [ka, ka + Kc) are left alone.
 // Items (problem, 128-row tile, 64-column tile) over the column tiles of up
 // to two ranges; persistent CTAs take items round-robin.  Per item the
 // contraction runs in chunks of 16 complex columns of A (32 reals of K):
@@ -437,7 +443,6 @@ gjw_gemm_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant
     for (int t = 0; t < my_items && ok; ++t) {
       int f, rt, ctile;
       item(t, f, rt, ctile);
-      const int* rowpiv = g.rowpiv + (size_t)f * b;
       for (int kc = 0; kc < nk; ++kc, ++gch) {
         const int s = gch % GG_STAGES, q = gch & 1;
         ok = gg_wait(&full_bar[s], (uint32_t)(gch / GG_STAGES) & 1u, abort_flag, g.tries);
@@ -448,18 +453,11 @@ gjw_gemm_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant
         unsigned char* ob = ops + q * OPB;
         unsigned char* pa[3] = {ob, ob + PB, ob + 2 * PB};
         unsigned char* pbp[3] = {ob + PIECES * PB, ob + (PIECES + 1) * PB, ob + (PIECES + 2) * PB};
-        const int kbase = g.ka + kc * GG_KC;  // first complex column of the chunk
         // A: 128 rows x 8 units of 4 reals; rotated order for distinct banks
         for (int it = ct_id; it < GG_RT * 8; it += GG_CONV) {
           const int row = (it & 7) + 8 * (it >> 6);
           const int p = (((it >> 3) & 7) + row) & 7;
-          float4 v = *reinterpret_cast<const float4*>(RA + row * 32 + 4 * p);
-          const int gr = rt * GG_RT + row;
-          if (gr < b) {
-            const int pc = rowpiv[gr] - (kbase + 2 * p);
-            if (pc == 0) v.x -= 1.f;
-            else if (pc == 1) v.z -= 1.f;
-          }
+          const float4 v = *reinterpret_cast<const float4*>(RA + row * 32 + 4 * p);
           tc::store_split<SPLIT>(v, pa, tc::kmajor_off32<SPLIT>(row, 4 * p));
         }
         // B: 64 complex columns j x 8 pairs of K rows -> real rows 2j, 2j+1
@@ -486,12 +484,16 @@ gjw_gemm_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant
       const int cb = ctile * GG_CT + half * 32;  // first complex column of this thread
       float2* Mrow = g.M + ((size_t)f * b + (row < b ? row : 0)) * b;
       const bool rv = row < b;
+      // a pivot row of the contraction's columns takes the product itself
+      // (E[p, P] B = T^{-1} B); every other row adds it
+      const int rp = rv ? g.rowpiv[(size_t)f * b + row] : -1;
+      const bool pivot_row = rp >= g.ka && rp < g.ka + g.Kc;
       float4 cm[16];
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int c = cb + 2 * u;
-        cm[u] = (rv && c < b) ? *reinterpret_cast<const float4*>(Mrow + c)
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        cm[u] = (rv && !pivot_row && c < b) ? *reinterpret_cast<const float4*>(Mrow + c)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       ok = gg_wait(&accfull[a], (uint32_t)(t >> 1) & 1u, abort_flag, g.tries);
       if (!ok) break;
@@ -517,8 +519,11 @@ gjw_gemm_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant
       if (rv) {
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
+          // the contraction's own columns (the panel, in the inner update)
+          // keep their values
           const int c = cb + 2 * u;
-          if (c < b) *reinterpret_cast<float4*>(Mrow + c) = cm[u];
+          if (c < b && !(c >= g.ka && c < g.ka + g.Kc))
+            *reinterpret_cast<float4*>(Mrow + c) = cm[u];
         }
       }
     }
@@ -600,7 +605,9 @@ rr_status launch_gemm(rr_factors* fa, const CUtensorMap* ta, const CUtensorMap* 
   const int nrt = (d.b + GG_RT - 1) / GG_RT;
   const long items = (long)fa->F * nrt * ((x1 - x0) + (y1 - y0));
   if (items <= 0) return RR_OK;
-  const int grid = (int)std::min<long>(items, num_sms(d.device));
+  // a few items per CTA, so CTAs retire during the launch and the second
+  // stream's panels find SMs as they free up
+  const int grid = (int)std::max<long>(1, std::min<long>(items, (items + 3) / 4));
   static bool attr = false;
   if (!attr) {
     RR_CUDA(cudaFuncSetAttribute(gjw_gemm_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -178,6 +178,7 @@ void info_reset(rr_info* info) {
   info->cqr_cond = 0.0;
   info->cqr_shifted = 0;
   info->refine_stagnated = 0;
+  info->first_residual = 0.0;
 }
 
 // x = A^{-1} b (or A^{-H} b) in FP64 [F][N][k], b != x, with FP64 iterative
@@ -261,6 +262,7 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
       if (!(r == r)) r = INFINITY;
       rel = std::max(rel, r);
     }
+    if (it == 0 && info) info->first_residual = std::max(info->first_residual, rel);
     if (tol <= 0.0 || rel <= tol) break;
     // The FP64 residual itself carries rounding of order u ||A|| ||x||; once a
     // correction no longer halves the residual, x is as accurate as that
