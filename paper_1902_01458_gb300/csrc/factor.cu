@@ -36,7 +36,8 @@ __device__ __forceinline__ int slotx(int dx, int dy) { return (dx + 1) * 3 + (dy
 // points) are staged once in shared memory, so every X row is read from
 // memory about once instead of once per coupled row; a row's stencil
 // coefficients are uniform across the CTA (broadcast loads).
-constexpr int SCHUR_Y = 8, SCHUR_THREADS = 256;
+// one thread per column of the tile: the block has CB threads
+constexpr int SCHUR_Y = 8;
 template <typename T> struct SchurCfg { static constexpr int CB = sizeof(T) == 4 ? 256 : 128; };
 template <typename T>
 __host__ __device__ constexpr size_t schur_smem(int q) {
@@ -44,7 +45,7 @@ __host__ __device__ constexpr size_t schur_smem(int q) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS)
+__global__ void __launch_bounds__(SchurCfg<T>::CB)
 schur_kernel(OpView op, const double2* __restrict__ shifts, int i,
              const C_t<T>* __restrict__ Xprev, size_t xstride, C_t<T>* __restrict__ M) {
   using C = C_t<T>;
@@ -62,7 +63,7 @@ schur_kernel(OpView op, const double2* __restrict__ shifts, int i,
   // stage X rows of y points y0 - 1 .. y0 + ny_blk (slot k <-> point y0 - 1 + k)
   if (Xp) {
     const int nslots = (ny_blk + 2) * q;
-    for (int e = threadIdx.x; e < nslots * CB; e += SCHUR_THREADS) {
+    for (int e = threadIdx.x; e < nslots * CB; e += CB) {
       const int sl = e / CB, cc = e - sl * CB;
       const int pt = sl / q, comp = sl - pt * q;
       // point y0 - 1 + pt, wrapped when y is periodic (outside the grid
@@ -825,7 +826,7 @@ void launch_schur(const OpView& ov, const double2* shifts, int i, const C_t<T>* 
     attr = true;
   }
   dim3 gs((ov.ny + SCHUR_Y - 1) / SCHUR_Y, (ov.b + CB - 1) / CB, F);
-  schur_kernel<T><<<gs, SCHUR_THREADS, smem, st>>>(ov, shifts, i, Xprev, xstride, M);
+  schur_kernel<T><<<gs, CB, smem, st>>>(ov, shifts, i, Xprev, xstride, M);
 }
 
 template <typename T, int NB>

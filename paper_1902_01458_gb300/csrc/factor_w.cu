@@ -83,16 +83,6 @@ __device__ __forceinline__ void gjw_store_row(float2* M, int b, int row, int k0,
     }
 }
 
-// pivot row after its step: every entry scaled by 1/pivot, the pivot column
-// holding 1/pivot itself
-__device__ __forceinline__ void gjw_scale_pivot(float2 (&x)[GW_NB], int J, float2 pinv,
-                                                const float2* prow) {
-#pragma unroll
-  for (int c = 0; c < GW_NB; ++c)
-    if (c != J) x[c] = cmul(prow[c], pinv);
-  x[J] = pinv;
-}
-
 template <int RPT>
 __global__ void __launch_bounds__(GW_PANEL_THREADS, 1)
 gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Mall,
@@ -119,15 +109,25 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
   bool e1 = a1 && rowpiv[r1] < 0;
   int col0 = -1, col1 = -1;
 
-#pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    if (j >= nbk) break;
+  // the step loop stays rolled (an unrolled one overflows the instruction
+  // cache: every warp would run the whole straight-line program once); the
+  // held rows are only indexed by compile-time column numbers, column j is
+  // picked by predicates
+#pragma unroll 1
+  for (int j = 0; j < nbk; ++j) {
     const int buf = j & 1;
+    float2 xj0 = make_float2(0.f, 0.f), xj1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      if (c == j) {
+        xj0 = x0[c];
+        if (RPT == 2) xj1 = x1[c];
+      }
     // this thread's best eligible row, then the warp's
-    float bv = e0 ? x0[j].x * x0[j].x + x0[j].y * x0[j].y : -1.f;
+    float bv = e0 ? xj0.x * xj0.x + xj0.y * xj0.y : -1.f;
     int bi = a0 ? r0 : 0x7fffffff;
     if (RPT == 2) {
-      const float v1 = e1 ? x1[j].x * x1[j].x + x1[j].y * x1[j].y : -1.f;
+      const float v1 = e1 ? xj1.x * xj1.x + xj1.y * xj1.y : -1.f;
       if (a1 && v1 > bv) { bv = v1; bi = r1; }
     }
     const int mine = bi;
@@ -169,33 +169,33 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
     const float pd = piv.x * piv.x + piv.y * piv.y;
     const float2 pinv = make_float2(piv.x / pd, -piv.y / pd);
     // every held row: x -= (x_j / pivot) * pivot row, x_j <- -x_j / pivot;
-    // the pivot row itself is left alone here and scaled below
+    // the pivot row itself is scaled by 1/pivot, its x_j <- 1/pivot
     const bool p0 = r0 == pi, p1 = RPT == 2 && r1 == pi;
-    const float2 m0 = p0 ? make_float2(0.f, 0.f) : cmul(x0[j], pinv);
-    const float2 m1 = (RPT == 2 && !p1) ? cmul(x1[j], pinv) : make_float2(0.f, 0.f);
+    const float2 m0 = cmul(xj0, pinv);
+    const float2 m1 = RPT == 2 ? cmul(xj1, pinv) : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int c = 0; c < NB; ++c)
-      if (c != j) {
-        const float2 p = prow[c];
-        x0[c].x = fmaf(-m0.x, p.x, fmaf(m0.y, p.y, x0[c].x));
-        x0[c].y = fmaf(-m0.x, p.y, fmaf(-m0.y, p.x, x0[c].y));
-        if (RPT == 2) {
-          x1[c].x = fmaf(-m1.x, p.x, fmaf(m1.y, p.y, x1[c].x));
-          x1[c].y = fmaf(-m1.x, p.y, fmaf(-m1.y, p.x, x1[c].y));
+    for (int c = 0; c < NB; ++c) {
+      const float2 p = prow[c];
+      const bool cj = c == j;
+      if (p0) {
+        x0[c] = cj ? pinv : cmul(p, pinv);
+      } else {
+        const float2 u = make_float2(fmaf(-m0.x, p.x, fmaf(m0.y, p.y, x0[c].x)),
+                                     fmaf(-m0.x, p.y, fmaf(-m0.y, p.x, x0[c].y)));
+        x0[c] = cj ? make_float2(-m0.x, -m0.y) : u;
+      }
+      if (RPT == 2) {
+        if (p1) {
+          x1[c] = cj ? pinv : cmul(p, pinv);
+        } else {
+          const float2 u = make_float2(fmaf(-m1.x, p.x, fmaf(m1.y, p.y, x1[c].x)),
+                                       fmaf(-m1.x, p.y, fmaf(-m1.y, p.x, x1[c].y)));
+          x1[c] = cj ? make_float2(-m1.x, -m1.y) : u;
         }
       }
-    x0[j] = make_float2(-m0.x, -m0.y);
-    if (RPT == 2) x1[j] = make_float2(-m1.x, -m1.y);
-    if (p0) {
-      gjw_scale_pivot(x0, j, pinv, prow);
-      e0 = false;
-      col0 = j;
     }
-    if (p1) {
-      gjw_scale_pivot(x1, j, pinv, prow);
-      e1 = false;
-      col1 = j;
-    }
+    if (p0) { e0 = false; col0 = j; }
+    if (p1) { e1 = false; col1 = j; }
   }
   // panel columns back in place; pivot bookkeeping
   if (a0) {
@@ -474,56 +474,68 @@ gjw_gemm_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant
     if (!ok) *abort_flag = 1;
   } else if (is_epi) {
     // ---------------------------------------------------------- epilogue
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its quadrant) in two
+    // 16-lane blocks, complex columns 32 (w / 4) .. + 31 of the tile, with
+    // the 16x256b fragment: thread t holds rows base + t/4 and base + t/4 + 8
+    // and complex columns 4 r + t % 4 (r = 0..7), so every global access of
+    // a warp covers 8 rows x 32 contiguous bytes
     const int lq = warp & 3, half = warp >> 2;
     bool ok = true;
     for (int t = 0; t < my_items && ok; ++t) {
       int f, rt, ctile;
       item(t, f, rt, ctile);
       const int a = t & 1;
-      const int row = rt * GG_RT + lq * 32 + lane;
-      const int cb = ctile * GG_CT + half * 32;  // first complex column of this thread
-      float2* Mrow = g.M + ((size_t)f * b + (row < b ? row : 0)) * b;
-      const bool rv = row < b;
-      // a pivot row of the contraction's columns takes the product itself
-      // (E[p, P] B = T^{-1} B); every other row adds it
-      const int rp = rv ? g.rowpiv[(size_t)f * b + row] : -1;
-      const bool pivot_row = rp >= g.ka && rp < g.ka + g.Kc;
-      float4 cm[16];
+      const int cb = ctile * GG_CT + half * 32 + (lane & 3);  // + 4 r
+      float2* Mf = g.M + (size_t)f * b * b;
+      const int* rpf = g.rowpiv + (size_t)f * b;
+      int row[4];
+      bool add[4];
+      float2 cm[4][8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int c = cb + 2 * u;
-        cm[u] = (rv && !pivot_row && c < b) ? *reinterpret_cast<const float4*>(Mrow + c)
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = 0; u < 4; ++u) {  // u = 2 * sub-block + (second row)
+        row[u] = rt * GG_RT + lq * 32 + 16 * (u >> 1) + (lane >> 2) + 8 * (u & 1);
+        // a pivot row of the contraction's columns takes the product itself
+        // (E[p, P] B = T^{-1} B); every other row adds it
+        const int rp = row[u] < b ? rpf[row[u]] : -1;
+        add[u] = !(rp >= g.ka && rp < g.ka + g.Kc);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int c = cb + 4 * r;
+          cm[u][r] = (row[u] < b && add[u] && c < b) ? Mf[(size_t)row[u] * b + c]
+                                                      : make_float2(0.f, 0.f);
+        }
       }
       ok = gg_wait(&accfull[a], (uint32_t)(t >> 1) & 1u, abort_flag, g.tries);
       if (!ok) break;
       tc::fence_after_sync();
 #pragma unroll
-      for (int grp = 0; grp < 4; ++grp) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)a * (2 * GG_CT) +
-                          (uint32_t)(half * 64 + grp * 16),
-                      v);
+      for (int sb = 0; sb < 2; ++sb) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float4 m = cm[4 * grp + u];
-          m.x += v[4 * u];
-          m.y += v[4 * u + 1];
-          m.z += v[4 * u + 2];
-          m.w += v[4 * u + 3];
-          cm[4 * grp + u] = m;
+        for (int hh = 0; hh < 2; ++hh) {
+          float v[16];
+          tc::tmem_ld_16x256b_x4(tmem + ((uint32_t)(lq * 32 + 16 * sb) << 16) +
+                                     (uint32_t)a * (2 * GG_CT) + (uint32_t)(half * 64 + hh * 32),
+                                 v);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            cm[2 * sb][4 * hh + r].x += v[4 * r];
+            cm[2 * sb][4 * hh + r].y += v[4 * r + 1];
+            cm[2 * sb + 1][4 * hh + r].x += v[4 * r + 2];
+            cm[2 * sb + 1][4 * hh + r].y += v[4 * r + 3];
+          }
         }
       }
       tc::fence_before_sync();
       gg_arrive(&accempty[a]);
-      if (rv) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
+      for (int u = 0; u < 4; ++u) {
+        if (row[u] >= b) continue;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
           // the contraction's own columns (the panel, in the inner update)
           // keep their values
-          const int c = cb + 2 * u;
-          if (c < b && !(c >= g.ka && c < g.ka + g.Kc))
-            *reinterpret_cast<float4*>(Mrow + c) = cm[u];
+          const int c = cb + 4 * r;
+          if (c < b && !(c >= g.ka && c < g.ka + g.Kc)) Mf[(size_t)row[u] * b + c] = cm[u][r];
         }
       }
     }
@@ -537,49 +549,68 @@ gjw_gemm_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant
 
 // ---------------------------------------------------------------- finalize
 // G_i[j][p_m] = M[p_j][m] (S^{-1} from the implicitly pivoted work matrix),
-// X_i = G_i C_i with C_i = -L_{i,i+1} (at most 3q entries per row).
-__global__ void gjw_finalize_kernel(OpView op, int i, int RB, const float2* __restrict__ Mall,
-                                    const int* __restrict__ pivslot_all, float2* __restrict__ Gi,
-                                    size_t gstride, float2* __restrict__ Xi, size_t xstride) {
+// X_i = G_i C_i with C_i = -L_{i,i+1} (at most 3q entries per column).  A CTA
+// gathers RB rows into shared memory (scattering the columns), writes them
+// as rows of G_i and forms the same rows of X_i; each thread owns fixed
+// columns of X_i, so the (up to 9) coupling coefficients of a column are
+// loaded once and reused for all RB rows.
+constexpr int FIN_THREADS = 256, FIN_CPT = 4;  // columns per thread (b <= 1024)
+
+__global__ void __launch_bounds__(FIN_THREADS)
+gjw_finalize_kernel(OpView op, int i, int RB, const float2* __restrict__ Mall,
+                    const int* __restrict__ pivslot_all, float2* __restrict__ Gi, size_t gstride,
+                    float2* __restrict__ Xi, size_t xstride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = op.b, q = op.q;
   float2* Gs = reinterpret_cast<float2*>(smem_raw);        // [RB][b]
   int* ps = reinterpret_cast<int*>(Gs + (size_t)RB * b);   // [b]
   const int f = blockIdx.y;
   const int r0 = blockIdx.x * RB;
+  const int nr = min(RB, b - r0);
   const float2* M = Mall + (size_t)f * b * b;
-  for (int c = threadIdx.x; c < b; c += blockDim.x) ps[c] = pivslot_all[(size_t)f * b + c];
+  for (int c = threadIdx.x; c < b; c += FIN_THREADS) ps[c] = pivslot_all[(size_t)f * b + c];
   __syncthreads();
-  for (int e = threadIdx.x; e < RB * b; e += blockDim.x) {
+  for (int e = threadIdx.x; e < nr * b; e += FIN_THREADS) {
     const int rr = e / b, c = e - rr * b;
-    const int r = r0 + rr;
-    if (r < b) Gs[rr * b + ps[c]] = M[(size_t)ps[r] * b + c];
+    Gs[rr * b + ps[c]] = M[(size_t)ps[r0 + rr] * b + c];
   }
   __syncthreads();
   float2* G = Gi + (size_t)f * gstride;
-  for (int e = threadIdx.x; e < RB * b; e += blockDim.x) {
+  for (int e = threadIdx.x; e < nr * b; e += FIN_THREADS) {
     const int rr = e / b, c = e - rr * b;
-    const int r = r0 + rr;
-    if (r < b) G[(size_t)r * b + c] = Gs[rr * b + c];
+    G[(size_t)(r0 + rr) * b + c] = Gs[rr * b + c];
   }
   if (Xi == nullptr) return;
   float2* X = Xi + (size_t)f * xstride;
-  for (int e = threadIdx.x; e < RB * b; e += blockDim.x) {
-    const int rr = e / b, c = e - rr * b;
-    const int r = r0 + rr;
-    if (r >= b) continue;
+#pragma unroll
+  for (int k = 0; k < FIN_CPT; ++k) {
+    const int c = threadIdx.x + k * FIN_THREADS;
+    if (c >= b) break;
+    // the coupling of column c: entries L[(i, m), (i + 1, c)] for the rows m
+    // of the y neighbours of c's point
     const int iyc = c / q, cc = c - iyc * q;
-    float2 s = make_float2(0.f, 0.f);
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int iym = nbr_y(iyc, -dy, op.ny, op.periodic);
-      if (iym < 0) continue;
-      for (int cm = 0; cm < q; ++cm) {
-        const int m = iym * q + cm;
-        const float a = op.coef32[((size_t)i * b + m) * op.S + ((2) * 3 + (dy + 1)) * q + cc];
-        if (a != 0.f) s = crfma(a, Gs[rr * b + m], s);
+    int mm[9];
+    float aa[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      mm[t] = 0;
+      aa[t] = 0.f;
+      if (t < 3 * q) {
+        const int dy = t / q - 1, cm = t - (t / q) * q;
+        const int iym = nbr_y(iyc, -dy, op.ny, op.periodic);
+        if (iym >= 0) {
+          mm[t] = iym * q + cm;
+          aa[t] = op.coef32[((size_t)i * b + mm[t]) * op.S + (2 * 3 + (dy + 1)) * q + cc];
+        }
       }
     }
-    X[(size_t)r * b + c] = make_float2(-s.x, -s.y);
+    for (int rr = 0; rr < nr; ++rr) {
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int t = 0; t < 9; ++t)
+        if (aa[t] != 0.f) s = crfma(aa[t], Gs[rr * b + mm[t]], s);
+      X[(size_t)(r0 + rr) * b + c] = make_float2(-s.x, -s.y);
+    }
   }
 }
 
@@ -634,8 +665,7 @@ rr_status factor_wide_impl(rr_factors* fa) {
   const CUtensorMap* tA = reinterpret_cast<const CUtensorMap*>(fa->wmap[0]);
   const CUtensorMap* tBin = reinterpret_cast<const CUtensorMap*>(fa->wmap[1]);
   const CUtensorMap* tBout = reinterpret_cast<const CUtensorMap*>(fa->wmap[2]);
-  int RB = 4;
-  while (RB > 1 && (size_t)RB * b * sizeof(float2) + b * sizeof(int) > 160 * 1024) RB >>= 1;
+  const int RB = 8;
   const size_t fsmem = (size_t)RB * b * sizeof(float2) + b * sizeof(int);
   RR_CUDA(cudaFuncSetAttribute(gjw_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)fsmem));
@@ -715,7 +745,7 @@ rr_status factor_wide_impl(rr_factors* fa) {
     }
     float2* Xi = (i + 1 < nx) ? X : nullptr;
     prof_begin(PROF_FINALIZE, st);
-    gjw_finalize_kernel<<<dim3((b + RB - 1) / RB, F), 256, fsmem, st>>>(
+    gjw_finalize_kernel<<<dim3((b + RB - 1) / RB, F), FIN_THREADS, fsmem, st>>>(
         ov, i, RB, M, fa->pivslot, G + (size_t)i * bb, (size_t)nx * bb, Xi, bb);
     prof_end(PROF_FINALIZE, st);
     RR_CUDA(cudaGetLastError());
