@@ -73,7 +73,7 @@ typedef enum {
 } rr_precision;
 
 /* Operator kinds (q = unknowns per grid point). */
-enum { RR_ADVDIFF_SCALAR = 1, RR_ISO_NS2D = 3 };
+enum { RR_ADVDIFF_SCALAR = 1, RR_ISO_NS2D = 3, RR_ISO_NS2D_KZ = 4 };
 
 /* Uniform grid of nx x ny interior nodes on [x0,x1] x [y0,y1].
  * Dirichlet directions have spacing L/(n+1) and zero ghost nodes; a periodic
@@ -92,7 +92,17 @@ enum { RR_ADVDIFF_SCALAR = 1, RR_ISO_NS2D = 3 };
  * coefficient folds onto it); a clear bit keeps the zero (Dirichlet) ghost.
  * All zero is the homogeneous Dirichlet operator; the paper's closure for
  * RR_ISO_NS2D is {1, 7, 1, 1} (p' = rho'/mach^2, so Neumann pressure is
- * Neumann rho').  The y masks must be zero when periodic_y is set. */
+ * Neumann rho').  The y masks must be zero when periodic_y is set.
+ *  RR_ISO_NS2D_KZ: the bi-global form of RR_ISO_NS2D (Sec. III.A/B, the
+ *    spanwise wavenumbers k_z): perturbations (rho', u', v', w') varying as
+ *    exp(i kz z) about the same z-invariant base flow with no spanwise
+ *    velocity, so d/dz -> i kz (continuity gains -rho i kz w', the
+ *    Laplacians -kz^2, the divergence i kz w', and the w' equation is
+ *    advection, -(c^2/rho) i kz rho' and the viscous terms).  L(kz) is
+ *    complex; with D = diag(1, 1, 1, i) per point, D^{-1} L D is real, and
+ *    the library factors and sweeps that real operator (R = D R~ D^{-1}
+ *    has the same singular values; every entry point takes and returns the
+ *    vectors of L itself).  q = 4, Neumann masks over 4 variables. */
 typedef struct {
   int kind;
   int nx, ny;
@@ -103,6 +113,7 @@ typedef struct {
   double sponge_max;
   double sponge_frac;
   int neumann[4];
+  double kz;        /* spanwise wavenumber (RR_ISO_NS2D_KZ only) */
 } rr_grid;
 
 /* Base-flow fields on the interior nodes, host pointers to nx*ny doubles
@@ -171,7 +182,8 @@ rr_status rr_apply(rr_operator* op, int nshift, const double* shifts, int k,
  * memory and synchronises its stream before returning, so it must not be
  * called on a capturing stream: it checks and returns RR_ERR_ARG.  All calls
  * share the one array, so calls that overlap on the GPU (other streams or
- * host threads) race on it. */
+ * host threads) race on it.  RR_ISO_NS2D_KZ operators: RR_ERR_UNSUPPORTED
+ * (their application goes through a temporary; use rr_apply). */
 #define RR_APPLY_STATIC_MAX_SHIFTS 4096
 rr_status rr_apply_static(rr_operator* op, int nshift, const double* shifts, int k,
                           int adjoint, const void* x, void* y, void* stream);
@@ -294,7 +306,8 @@ rr_status rr_test_matrix(int nshift, int n, int k, const uint64_t* seeds,
  * ACCUMULATED into (zero it first; the rho part stays untouched for
  * RR_ADVDIFF_SCALAR).  The result is the gradient of the true leading gains
  * to the accuracy of the given triplets: exact triplets give the exact
- * gradient.  Errors: RR_ERR_ARG (J outside [1, k], k outside [1, 64], null),
+ * gradient.  RR_ISO_NS2D_KZ operators: RR_ERR_UNSUPPORTED.
+ * Errors: RR_ERR_ARG (J outside [1, k], k outside [1, 64], null),
  * RR_ERR_NOCONV (grad still accumulated), RR_ERR_CUDA. */
 rr_status rr_gain_grad(rr_factors* f, int k, int J, const void* U, const void* V,
                        const double* sigma, double refine_tol, int max_refine,

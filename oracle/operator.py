@@ -14,6 +14,15 @@ follow the reading fixed for this project:
             + (1/(rho Re)) (lap u' + 1/3 grad div u')
             - (rho'/rho^2)(1/Re)(lap U + 1/3 grad div U)
   plus the sponge -s_s q' on every variable.
+* bi-global isothermal Navier-Stokes in (rho', u', v', w') (q = 4): the
+  perturbations vary as exp(i kz z) about a flow (rho, U, V, W = 0) that does
+  not depend on z (Sec. III.A/B: a spanwise wavenumber kz), so d/dz -> i kz:
+      rho': as above - rho i kz w'
+      u', v': as above with lap -> lap - kz^2 and div u' -> div u' + i kz w'
+      w'  : -(U.grad) w' - (c^2/rho) i kz rho'
+            + (1/(rho Re)) (lap w' - kz^2 w' + 1/3 i kz (div u' + i kz w'))
+  L is complex; at kz = 0 it is the (rho, u, v) operator plus a decoupled
+  advection-diffusion equation for w'.
 
 Discretisation: 2nd-order central differences on nx x ny interior nodes with
 homogeneous Dirichlet ghost nodes (or periodic y); the cross derivative is
@@ -185,6 +194,8 @@ def assemble(grid, flow) -> sp.csr_matrix:
         nu = 1.0 / grid.re
         return (adv(0) + nu * lap - dg(sig)).tocsr()
 
+    if grid.q == 4:
+        return _assemble_kz(grid, flow, ops, adv, dg, sig)
     c2 = 1.0 / grid.mach ** 2
     re = grid.re
     dU = field_derivatives(grid, U)
@@ -216,6 +227,60 @@ def assemble(grid, flow) -> sp.csr_matrix:
         for b in range(3):
             e = sp.csr_matrix(([1.0], ([a], [b])), shape=(3, 3))
             term = sp.kron(blk[a][b], e, format="csr")
+            L = term if L is None else L + term
+    L = L.tocsr()
+    L.eliminate_zeros()
+    return L
+
+
+def _assemble_kz(grid, flow, ops, adv, dg, sig) -> sp.csr_matrix:
+    """Complex L(kz) of the bi-global operator, (rho', u', v', w')."""
+    U, V, R = flow.u, flow.v, flow.rho
+    c2 = 1.0 / grid.mach ** 2
+    re = grid.re
+    kz = float(grid.kz)
+    ik = 1j * kz
+    dU = field_derivatives(grid, U)
+    dV = field_derivatives(grid, V)
+    dR = field_derivatives(grid, R)
+    divU = dU["x"] + dV["y"]
+    visc = dg(1.0 / (R * re))
+    fu = (dU["xx"] + dU["yy"] + (dU["xx"] + dV["xy"]) / 3.0) / re
+    fv = (dV["xx"] + dV["yy"] + (dU["xy"] + dV["yy"]) / 3.0) / re
+    n = grid.npts
+    eye = sp.identity(n, format="csr")
+    o0, o1, o2, o3 = ops
+    blk = [[None] * 4 for _ in range(4)]
+    # continuity: -(U.grad) rho' - rho' div U - u'.grad rho - rho (div u' + i kz w')
+    blk[0][0] = adv(0) - dg(divU) - dg(sig)
+    blk[0][1] = -dg(dR["x"]) - dg(R) @ o1["Dx"]
+    blk[0][2] = -dg(dR["y"]) - dg(R) @ o2["Dy"]
+    blk[0][3] = -ik * dg(R)
+    # x momentum: the 2-D terms, lap -> lap - kz^2, div u' -> div u' + i kz w'
+    blk[1][0] = (-c2 * dg(1.0 / R) @ o0["Dx"] + c2 * dg(dR["x"] / R ** 2)
+                 - dg(fu / R ** 2))
+    blk[1][1] = (adv(1) - dg(dU["x"]) + visc @ (o1["lap"] - kz ** 2 * eye + o1["Dxx"] / 3.0)
+                 - dg(sig))
+    blk[1][2] = -dg(dU["y"]) + visc @ (o2["Dxy"] / 3.0)
+    blk[1][3] = visc @ (ik / 3.0 * o3["Dx"])
+    # y momentum
+    blk[2][0] = (-c2 * dg(1.0 / R) @ o0["Dy"] + c2 * dg(dR["y"] / R ** 2)
+                 - dg(fv / R ** 2))
+    blk[2][1] = -dg(dV["x"]) + visc @ (o1["Dxy"] / 3.0)
+    blk[2][2] = (adv(2) - dg(dV["y"]) + visc @ (o2["lap"] - kz ** 2 * eye + o2["Dyy"] / 3.0)
+                 - dg(sig))
+    blk[2][3] = visc @ (ik / 3.0 * o3["Dy"])
+    # z momentum (W = 0): -(U.grad) w' - (c^2/rho) i kz rho'
+    #   + (1/(rho Re)) (lap w' - kz^2 w' + 1/3 i kz (div u' + i kz w'))
+    blk[3][0] = -ik * c2 * dg(1.0 / R)
+    blk[3][1] = visc @ (ik / 3.0 * o1["Dx"])
+    blk[3][2] = visc @ (ik / 3.0 * o2["Dy"])
+    blk[3][3] = adv(3) + visc @ (o3["lap"] - (4.0 / 3.0) * kz ** 2 * eye) - dg(sig)
+    L = None
+    for a in range(4):
+        for b in range(4):
+            e = sp.csr_matrix(([1.0], ([a], [b])), shape=(4, 4))
+            term = sp.kron(sp.csr_matrix(blk[a][b], dtype=np.complex128), e, format="csr")
             L = term if L is None else L + term
     L = L.tocsr()
     L.eliminate_zeros()

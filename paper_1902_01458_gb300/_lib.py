@@ -21,7 +21,7 @@ STATUS = {0: "RR_OK", 1: "RR_ERR_ARG", 2: "RR_ERR_NOMEM", 3: "RR_ERR_SINGULAR",
           4: "RR_ERR_NOCONV", 5: "RR_ERR_RANK", 6: "RR_ERR_TIMEOUT",
           7: "RR_ERR_CUDA", 8: "RR_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_simt": 2, "fp32_bf16x3": 3, "fp32_bf16x6": 4}
-ADVDIFF, NS2D = 1, 3
+ADVDIFF, NS2D, NS2D_KZ = 1, 3, 4
 
 
 class RRError(RuntimeError):
@@ -37,7 +37,8 @@ class rr_grid(ctypes.Structure):
                 ("x1", ctypes.c_double), ("y0", ctypes.c_double),
                 ("y1", ctypes.c_double), ("re", ctypes.c_double),
                 ("mach", ctypes.c_double), ("sponge_max", ctypes.c_double),
-                ("sponge_frac", ctypes.c_double), ("neumann", ctypes.c_int * 4)]
+                ("sponge_frac", ctypes.c_double), ("neumann", ctypes.c_int * 4),
+                ("kz", ctypes.c_double)]
 
 
 class rr_baseflow(ctypes.Structure):
@@ -239,7 +240,8 @@ def rr_create_operator(grid, rho, u, v, weights=None, device: int = 0):
                 float(grid.re), float(getattr(grid, "mach", 0.0)),
                 float(getattr(grid, "sponge_max", 0.0)),
                 float(getattr(grid, "sponge_frac", 0.1)),
-                (ctypes.c_int * 4)(*[int(m) for m in getattr(grid, "neumann", (0, 0, 0, 0))]))
+                (ctypes.c_int * 4)(*[int(m) for m in getattr(grid, "neumann", (0, 0, 0, 0))]),
+                float(getattr(grid, "kz", 0.0)))
     keep = []
 
     def arr(a):

@@ -74,6 +74,19 @@ __global__ void scale_rows_kernel(int F, int N, int k, const double* __restrict_
   }
 }
 
+// rows of variable 3 of every point (q = 4) times i (sign > 0) or -i: the
+// similarity D = diag(1, 1, 1, i) between the bi-global L and its real form
+__global__ void kz_phase_kernel(int F, int N, int k, int sign, double2* __restrict__ x) {
+  const size_t total = (size_t)F * N * k;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t n = (e / k) % N;
+    if ((n & 3) != 3) continue;
+    const double2 v = x[e];
+    x[e] = sign > 0 ? make_double2(-v.y, v.x) : make_double2(v.y, -v.x);
+  }
+}
+
 __global__ void d2f_kernel(size_t n, const double2* __restrict__ in, float2* __restrict__ out) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x)
@@ -559,6 +572,14 @@ rr_status launch_scale_rows(int F, int N, int k, const double* w, double2* x, cu
   if (!w) return RR_OK;
   prof_count(1);
   scale_rows_kernel<<<grid1d((size_t)F * N * k, 256), 256, 0, st>>>(F, N, k, w, x);
+  RR_CUDA(cudaGetLastError());
+  return RR_OK;
+}
+
+rr_status launch_kz_phase(int F, int N, int k, int q, int sign, double2* x, cudaStream_t st) {
+  if (q != 4) return RR_OK;
+  prof_count(1);
+  kz_phase_kernel<<<grid1d((size_t)F * N * k, 256), 256, 0, st>>>(F, N, k, sign, x);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }

@@ -85,7 +85,7 @@ schur_kernel(OpView op, const double2* __restrict__ shifts, int i,
       const size_t cf = ((size_t)i * b + r) * op.S;
       C val = (r == c) ? sh : czero<C>();
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
+      for (int t = 0; t < 12; ++t) {  // 3 y neighbours x q <= 4 variables
         if (t >= 3 * q) break;
         const int dy = t / q - 1, cp = t - (t / q) * q;
         const int jy = nbr_y(iy, dy, ny, op.periodic);
@@ -822,7 +822,7 @@ void launch_schur(const OpView& ov, const double2* shifts, int i, const C_t<T>* 
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(schur_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)schur_smem<T>(3));
+                         (int)schur_smem<T>(4));
     attr = true;
   }
   dim3 gs((ov.ny + SCHUR_Y - 1) / SCHUR_Y, (ov.b + CB - 1) / CB, F);

@@ -48,8 +48,8 @@ constexpr int GW_BIN_ROWS = 32;    // row pitch per problem of the inner update'
 
 // ------------------------------------------------------------------- panel
 // Eliminates columns [k0, k0 + nbk) of every row of M (problem = blockIdx.x).
-// Thread t holds the nbk entries of rows t and t + blockDim.x (RPT = 2) or
-// of row t (RPT = 1) in registers.  Per column j: each warp finds its best
+// Thread t holds the nbk entries of row t (RPT = 1; RPT = 2 would hold rows
+// t and t + blockDim.x) in registers.  Per column j: each warp finds its best
 // eligible row (largest |.|^2, lowest row on ties) and the winning lane
 // publishes that whole row in shared memory; after one block barrier every
 // warp reduces the per-warp candidates itself, reads the pivot row from
@@ -58,29 +58,32 @@ constexpr int GW_BIN_ROWS = 32;    // row pitch per problem of the inner update'
 // pivoted here, pivslot[k0 + j] = pivot row of column k0 + j, and Bin =
 // M_old[P, slab] with the panel's own columns (and columns outside the slab)
 // zero: the right operand of the inner update.
-constexpr int GW_PANEL_THREADS = GW_PANEL_MAX / 2;
+constexpr int GW_PANEL_THREADS = GW_PANEL_MAX;  // one row per thread up to 768 rows
 
-__device__ __forceinline__ void gjw_load_row(const float2* M, int b, int row, int k0, int nbk,
-                                             bool ok, float2 (&x)[GW_NB]) {
-  const float4* src = reinterpret_cast<const float4*>(M + (size_t)(ok ? row : 0) * b + k0);
+// rotate a held row left by one place (column c + 1 moves to register c)
+__device__ __forceinline__ void gjw_rotate(float2 (&x)[GW_NB]) {
+  const float2 first = x[0];
 #pragma unroll
-  for (int c = 0; c < GW_NB; c += 2) {
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ok && c < nbk) v = src[c >> 1];
-    x[c] = make_float2(v.x, v.y);
-    x[c + 1] = (c + 1 < nbk) ? make_float2(v.z, v.w) : make_float2(0.f, 0.f);
-  }
+  for (int c = 0; c + 1 < GW_NB; ++c) x[c] = x[c + 1];
+  x[GW_NB - 1] = first;
 }
 
-__device__ __forceinline__ void gjw_store_row(float2* M, int b, int row, int k0, int nbk,
-                                              const float2 (&x)[GW_NB]) {
-  float4* dst = reinterpret_cast<float4*>(M + (size_t)row * b + k0);
+// staged panel rows: 16 complex padded to 18 (row pitch 144 bytes, so the
+// threads of a warp, one row each, spread over the banks)
+constexpr int GW_STAGE_LD = GW_NB + 2;
+
+__device__ __forceinline__ void gjw_take_row(const float2* stage, int row, bool ok,
+                                             float2 (&x)[GW_NB]) {
 #pragma unroll
-  for (int c = 0; c < GW_NB; c += 2)
-    if (c < nbk) {
-      if (c + 1 < nbk) dst[c >> 1] = make_float4(x[c].x, x[c].y, x[c + 1].x, x[c + 1].y);
-      else reinterpret_cast<float2*>(dst)[c] = x[c];
-    }
+  for (int c = 0; c < GW_NB; ++c)
+    x[c] = ok ? stage[row * GW_STAGE_LD + c] : make_float2(0.f, 0.f);
+}
+
+__device__ __forceinline__ void gjw_put_row(float2* stage, int row, bool ok,
+                                            const float2 (&x)[GW_NB]) {
+  if (!ok) return;
+#pragma unroll
+  for (int c = 0; c < GW_NB; ++c) stage[row * GW_STAGE_LD + c] = x[c];
 }
 
 template <int RPT>
@@ -94,6 +97,7 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
   __shared__ float candv[2][MAXW];
   __shared__ int candi[2][MAXW];
   __shared__ int piv_sm[NB];
+  extern __shared__ __align__(16) float2 stage[];  // [b][GW_STAGE_LD]
   const int f = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int nt = blockDim.x, nw = nt >> 5;
@@ -103,31 +107,35 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
   int* rowpiv = rowpiv_all + (size_t)f * b;
 
   float2 x0[NB], x1[NB];
-  gjw_load_row(M, b, r0, k0, nbk, a0, x0);
-  if (RPT == 2) gjw_load_row(M, b, r1, k0, nbk, a1, x1);
+  // the panel M[:, K] through shared memory: each warp reads whole 128-byte
+  // row segments (8 lanes per row), then every thread takes its row
+  for (int e = t; e < b * (NB / 2); e += nt) {
+    const int row = e / (NB / 2), u = e - row * (NB / 2);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (2 * u < nbk) v = reinterpret_cast<const float4*>(M + (size_t)row * b + k0)[u];
+    *reinterpret_cast<float4*>(&stage[row * GW_STAGE_LD + 2 * u]) = v;
+  }
+  __syncthreads();
+  gjw_take_row(stage, r0, a0, x0);
+  if (RPT == 2) gjw_take_row(stage, r1, a1, x1);
   bool e0 = a0 && rowpiv[r0] < 0;
   bool e1 = a1 && rowpiv[r1] < 0;
   int col0 = -1, col1 = -1;
 
-  // the step loop stays rolled (an unrolled one overflows the instruction
-  // cache: every warp would run the whole straight-line program once); the
-  // held rows are only indexed by compile-time column numbers, column j is
-  // picked by predicates
+  // The step loop stays rolled (an unrolled one overflows the instruction
+  // cache: every warp would run the whole straight-line program once).  The
+  // held rows are kept rotated so that the column being eliminated is always
+  // register 0: after each step every row (and so the published pivot row)
+  // rotates left by one, and after nbk == NB steps the order is the original
+  // one again (a ragged last panel rotates the rest at the end).
 #pragma unroll 1
   for (int j = 0; j < nbk; ++j) {
     const int buf = j & 1;
-    float2 xj0 = make_float2(0.f, 0.f), xj1 = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int c = 0; c < NB; ++c)
-      if (c == j) {
-        xj0 = x0[c];
-        if (RPT == 2) xj1 = x1[c];
-      }
     // this thread's best eligible row, then the warp's
-    float bv = e0 ? xj0.x * xj0.x + xj0.y * xj0.y : -1.f;
+    float bv = e0 ? x0[0].x * x0[0].x + x0[0].y * x0[0].y : -1.f;
     int bi = a0 ? r0 : 0x7fffffff;
     if (RPT == 2) {
-      const float v1 = e1 ? xj1.x * xj1.x + xj1.y * xj1.y : -1.f;
+      const float v1 = e1 ? x1[0].x * x1[0].x + x1[0].y * x1[0].y : -1.f;
       if (a1 && v1 > bv) { bv = v1; bi = r1; }
     }
     const int mine = bi;
@@ -164,49 +172,69 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
       if (!(pv > 0.f)) flag[f] = 1;
     }
     const float2* prow = cand[buf][pw];
-    float2 piv = prow[j];
+    float2 piv = prow[0];
     if (piv.x * piv.x + piv.y * piv.y == 0.f) piv = make_float2(1e-18f, 0.f);
     const float pd = piv.x * piv.x + piv.y * piv.y;
     const float2 pinv = make_float2(piv.x / pd, -piv.y / pd);
-    // every held row: x -= (x_j / pivot) * pivot row, x_j <- -x_j / pivot;
-    // the pivot row itself is scaled by 1/pivot, its x_j <- 1/pivot
+    // every held row: x -= (x_0 / pivot) * pivot row, x_0 <- -x_0 / pivot;
+    // the pivot row itself is scaled by 1/pivot, its x_0 <- 1/pivot
     const bool p0 = r0 == pi, p1 = RPT == 2 && r1 == pi;
-    const float2 m0 = cmul(xj0, pinv);
-    const float2 m1 = RPT == 2 ? cmul(xj1, pinv) : make_float2(0.f, 0.f);
+    if (!p0) {
+      const float2 m0 = cmul(x0[0], pinv);
 #pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      const float2 p = prow[c];
-      const bool cj = c == j;
-      if (p0) {
-        x0[c] = cj ? pinv : cmul(p, pinv);
-      } else {
-        const float2 u = make_float2(fmaf(-m0.x, p.x, fmaf(m0.y, p.y, x0[c].x)),
-                                     fmaf(-m0.x, p.y, fmaf(-m0.y, p.x, x0[c].y)));
-        x0[c] = cj ? make_float2(-m0.x, -m0.y) : u;
+      for (int c = 1; c < NB; ++c) {
+        const float2 p = prow[c];
+        x0[c].x = fmaf(-m0.x, p.x, fmaf(m0.y, p.y, x0[c].x));
+        x0[c].y = fmaf(-m0.x, p.y, fmaf(-m0.y, p.x, x0[c].y));
       }
-      if (RPT == 2) {
-        if (p1) {
-          x1[c] = cj ? pinv : cmul(p, pinv);
-        } else {
-          const float2 u = make_float2(fmaf(-m1.x, p.x, fmaf(m1.y, p.y, x1[c].x)),
-                                       fmaf(-m1.x, p.y, fmaf(-m1.y, p.x, x1[c].y)));
-          x1[c] = cj ? make_float2(-m1.x, -m1.y) : u;
+      x0[0] = make_float2(-m0.x, -m0.y);
+    } else {
+#pragma unroll
+      for (int c = 1; c < NB; ++c) x0[c] = cmul(prow[c], pinv);
+      x0[0] = pinv;
+      e0 = false;
+      col0 = j;
+    }
+    if (RPT == 2) {
+      if (!p1) {
+        const float2 m1 = cmul(x1[0], pinv);
+#pragma unroll
+        for (int c = 1; c < NB; ++c) {
+          const float2 p = prow[c];
+          x1[c].x = fmaf(-m1.x, p.x, fmaf(m1.y, p.y, x1[c].x));
+          x1[c].y = fmaf(-m1.x, p.y, fmaf(-m1.y, p.x, x1[c].y));
         }
+        x1[0] = make_float2(-m1.x, -m1.y);
+      } else {
+#pragma unroll
+        for (int c = 1; c < NB; ++c) x1[c] = cmul(prow[c], pinv);
+        x1[0] = pinv;
+        e1 = false;
+        col1 = j;
       }
     }
-    if (p0) { e0 = false; col0 = j; }
-    if (p1) { e1 = false; col1 = j; }
+    gjw_rotate(x0);
+    if (RPT == 2) gjw_rotate(x1);
   }
-  // panel columns back in place; pivot bookkeeping
-  if (a0) {
-    gjw_store_row(M, b, r0, k0, nbk, x0);
-    if (col0 >= 0) rowpiv[r0] = k0 + col0;
+  // a ragged panel (nbk < NB steps) rotates the remaining NB - nbk places
+#pragma unroll 1
+  for (int j = nbk; j < NB; ++j) {
+    gjw_rotate(x0);
+    if (RPT == 2) gjw_rotate(x1);
   }
-  if (a1) {
-    gjw_store_row(M, b, r1, k0, nbk, x1);
-    if (col1 >= 0) rowpiv[r1] = k0 + col1;
-  }
+  // panel columns back in place (through shared memory, coalesced); pivot
+  // bookkeeping
+  gjw_put_row(stage, r0, a0, x0);
+  if (RPT == 2) gjw_put_row(stage, r1, a1, x1);
+  if (a0 && col0 >= 0) rowpiv[r0] = k0 + col0;
+  if (a1 && col1 >= 0) rowpiv[r1] = k0 + col1;
   __syncthreads();
+  for (int e = t; e < b * (NB / 2); e += nt) {
+    const int row = e / (NB / 2), u = e - row * (NB / 2);
+    if (2 * u < nbk)
+      reinterpret_cast<float4*>(M + (size_t)row * b + k0)[u] =
+          *reinterpret_cast<const float4*>(&stage[row * GW_STAGE_LD + 2 * u]);
+  }
   if (t < nbk) pivslot_all[(size_t)f * b + k0 + t] = piv_sm[t];
   // Bin[f][c][m] = M_old[P_c][m] for m in the slab outside the panel, else 0
   // (columns outside the slab are never read by the inner update)
@@ -552,7 +580,7 @@ gjw_gemm_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant
 // X_i = G_i C_i with C_i = -L_{i,i+1} (at most 3q entries per column).  A CTA
 // gathers RB rows into shared memory (scattering the columns), writes them
 // as rows of G_i and forms the same rows of X_i; each thread owns fixed
-// columns of X_i, so the (up to 9) coupling coefficients of a column are
+// columns of X_i, so the (up to 3q) coupling coefficients of a column are
 // loaded once and reused for all RB rows.
 constexpr int FIN_THREADS = 256, FIN_CPT = 4;  // columns per thread (b <= 1024)
 
@@ -589,10 +617,10 @@ gjw_finalize_kernel(OpView op, int i, int RB, const float2* __restrict__ Mall,
     // the coupling of column c: entries L[(i, m), (i + 1, c)] for the rows m
     // of the y neighbours of c's point
     const int iyc = c / q, cc = c - iyc * q;
-    int mm[9];
-    float aa[9];
+    int mm[12];  // 3 y neighbours x q <= 4 variables
+    float aa[12];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
+    for (int t = 0; t < 12; ++t) {
       mm[t] = 0;
       aa[t] = 0.f;
       if (t < 3 * q) {
@@ -607,7 +635,7 @@ gjw_finalize_kernel(OpView op, int i, int RB, const float2* __restrict__ Mall,
     for (int rr = 0; rr < nr; ++rr) {
       float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int t = 0; t < 9; ++t)
+      for (int t = 0; t < 12; ++t)
         if (aa[t] != 0.f) s = crfma(aa[t], Gs[rr * b + mm[t]], s);
       X[(size_t)(r0 + rr) * b + c] = make_float2(-s.x, -s.y);
     }
@@ -636,9 +664,11 @@ rr_status launch_gemm(rr_factors* fa, const CUtensorMap* ta, const CUtensorMap* 
   const int nrt = (d.b + GG_RT - 1) / GG_RT;
   const long items = (long)fa->F * nrt * ((x1 - x0) + (y1 - y0));
   if (items <= 0) return RR_OK;
-  // a few items per CTA, so CTAs retire during the launch and the second
-  // stream's panels find SMs as they free up
-  const int grid = (int)std::max<long>(1, std::min<long>(items, (items + 3) / 4));
+  // small launches (up to 8 items per SM): one wave of persistent CTAs;
+  // large ones: about four items per CTA, so CTAs retire during the launch
+  // and the second stream's panels find SMs as they free up
+  const long nsm = num_sms(d.device);
+  const int grid = (int)(items <= 8 * nsm ? std::min<long>(items, nsm) : (items + 3) / 4);
   static bool attr = false;
   if (!attr) {
     RR_CUDA(cudaFuncSetAttribute(gjw_gemm_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -670,8 +700,10 @@ rr_status factor_wide_impl(rr_factors* fa) {
   RR_CUDA(cudaFuncSetAttribute(gjw_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)fsmem));
   const int nct_all = (b + GG_CT - 1) / GG_CT;
-  const int rpt = b > GW_PANEL_THREADS ? 2 : 1;
-  const int pthreads = ((b + rpt - 1) / rpt + 31) & ~31;
+  const int pthreads = (b + 31) & ~31;  // one row per thread
+  const size_t psmem = (size_t)b * GW_STAGE_LD * sizeof(float2);
+  RR_CUDA(cudaFuncSetAttribute(gjw_panel_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)psmem));
   const int ncols = fa->factor_cols > 0 ? std::min(fa->factor_cols, nx) : nx;
   for (int i = 0; i < ncols; ++i) {
     prof_count(1);
@@ -685,14 +717,9 @@ rr_status factor_wide_impl(rr_factors* fa) {
       for (int k0 = c0; k0 < c1; k0 += GW_NB) {
         const int nbk = std::min(GW_NB, c1 - k0);
         prof_begin(PROF_PANEL, sx);
-        if (rpt == 2)
-          gjw_panel_kernel<2><<<F, pthreads, 0, sx>>>(b, k0, nbk, c0, c1, M, fa->rowpiv,
-                                                      fa->pivslot,
-                                                      reinterpret_cast<float2*>(fa->Bbuf), fa->flag);
-        else
-          gjw_panel_kernel<1><<<F, pthreads, 0, sx>>>(b, k0, nbk, c0, c1, M, fa->rowpiv,
-                                                      fa->pivslot,
-                                                      reinterpret_cast<float2*>(fa->Bbuf), fa->flag);
+        gjw_panel_kernel<1><<<F, pthreads, psmem, sx>>>(b, k0, nbk, c0, c1, M, fa->rowpiv,
+                                                    fa->pivslot,
+                                                    reinterpret_cast<float2*>(fa->Bbuf), fa->flag);
         prof_end(PROF_PANEL, sx);
         // the rest of the slab: its column tiles (the panel's own columns get
         // zero from Bin)

@@ -50,7 +50,7 @@ struct Field {
 
 struct AsmParams {
   int kind, q, nx, ny, periodic;
-  double dx, dy, x0, x1, y0, y1, re, c2, smax, sfrac;
+  double dx, dy, x0, x1, y0, y1, re, c2, smax, sfrac, kz;
   int neu[4];  // Neumann variable masks of the sides x0, x1, y0, y1
 };
 
@@ -81,10 +81,10 @@ __global__ void assemble_kernel(AsmParams p, const double* __restrict__ flow,
   if (pt >= npts) return;
   int i = pt / p.ny, j = pt % p.ny;
   const int q = p.q, S = 9 * q;
-  double c[3][9][3];
-  for (int a = 0; a < 3; ++a)
+  double c[4][9][4];
+  for (int a = 0; a < 4; ++a)
     for (int s = 0; s < 9; ++s)
-      for (int b = 0; b < 3; ++b) c[a][s][b] = 0.0;
+      for (int b = 0; b < 4; ++b) c[a][s][b] = 0.0;
 
   Field R{flow, p.nx, p.ny, p.periodic, p.dx, p.dy};
   Field U{flow + npts, p.nx, p.ny, p.periodic, p.dx, p.dy};
@@ -157,6 +157,25 @@ __global__ void assemble_kernel(AsmParams p, const double* __restrict__ flow,
     addDx(2, 2, -u); addDy(2, 2, -v);
     addDxx(2, 2, mu); addDyy(2, 2, mu * (4.0 / 3.0));
     addDiag(2, 2, -Vy - sg);
+    if (p.kind == RR_ISO_NS2D_KZ) {
+      // bi-global terms (d/dz -> i kz, no spanwise base velocity), written
+      // for the real operator D^{-1} L D, D = diag(1, 1, 1, i): variable 3
+      // is w' / i, so every i kz coupling with w' becomes real
+      const double kz = p.kz;
+      addDiag(0, 3, rho * kz);                       // -rho i kz w'
+      addDiag(1, 1, -mu * kz * kz);                  // -kz^2 u'
+      addDx(1, 3, -mu * kz / 3.0);                   // (1/3) d/dx (i kz w')
+      addDiag(2, 2, -mu * kz * kz);
+      addDy(2, 3, -mu * kz / 3.0);
+      // z-momentum: -(U.grad) w' - (c^2/rho) i kz rho'
+      //   + mu (lap w' - kz^2 w' + (1/3) i kz (div u' + i kz w'))
+      addDiag(3, 0, -c2 / rho * kz);
+      addDx(3, 1, mu * kz / 3.0);
+      addDy(3, 2, mu * kz / 3.0);
+      addDx(3, 3, -u); addDy(3, 3, -v);
+      addDxx(3, 3, mu); addDyy(3, 3, mu);
+      addDiag(3, 3, -(4.0 / 3.0) * mu * kz * kz - sg);
+    }
   }
 
   // boundary closure: a ghost neighbour of variable b is zero (Dirichlet) or,
@@ -434,7 +453,8 @@ rr_status launch_assemble(OpDev& d, const rr_grid& g, cudaStream_t st) {
   AsmParams p;
   p.kind = g.kind; p.q = d.q; p.nx = d.nx; p.ny = d.ny; p.periodic = d.periodic;
   p.dx = d.dx; p.dy = d.dy; p.x0 = g.x0; p.x1 = g.x1; p.y0 = g.y0; p.y1 = g.y1;
-  p.re = g.re; p.c2 = (g.kind == RR_ISO_NS2D) ? 1.0 / (g.mach * g.mach) : 0.0;
+  p.re = g.re; p.c2 = (g.kind != RR_ADVDIFF_SCALAR) ? 1.0 / (g.mach * g.mach) : 0.0;
+  p.kz = g.kind == RR_ISO_NS2D_KZ ? g.kz : 0.0;
   p.smax = g.sponge_max; p.sfrac = g.sponge_frac;
   for (int e = 0; e < 4; ++e) p.neu[e] = g.neumann[e];
   int npts = d.nx * d.ny;
@@ -464,7 +484,10 @@ rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int 
                        const double2* x, double2* y, cudaStream_t st) {
   prof_count(1);
   if (!adjoint) return launch_ell<false>(d, F, shifts, k, nullptr, x, y, st);
-  if (d.q == 3)
+  if (d.q == 4)
+    apply_adjoint_kernel<false, 4><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k,
+                                                                        nullptr, x, y);
+  else if (d.q == 3)
     apply_adjoint_kernel<false, 3><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k,
                                                                         nullptr, x, y);
   else
@@ -509,6 +532,12 @@ extern "C" rr_status rr_apply_static(rr_operator* op, int nshift, const double* 
   if (x == y) {
     set_error("rr_apply_static: x and y must be distinct");
     return RR_ERR_ARG;
+  }
+  if (op->d.q == 4) {
+    // the bi-global operator is applied through its real similar form, which
+    // needs a temporary for D^{-1} x: use rr_apply
+    set_error("rr_apply_static: not implemented for the bi-global operator (use rr_apply)");
+    return RR_ERR_UNSUPPORTED;
   }
   const int dev = op->d.device;
   if (dev < 0 || dev >= kMaxDevices) {
@@ -565,7 +594,10 @@ rr_status launch_residual(const OpDev& d, int F, const double2* shifts, int k, i
     prof_end(PROF_RESIDUAL, st);
     return s;
   }
-  if (d.q == 3)
+  if (d.q == 4)
+    apply_adjoint_kernel<true, 4><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, b, x,
+                                                                       r);
+  else if (d.q == 3)
     apply_adjoint_kernel<true, 3><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, b, x,
                                                                        r);
   else

@@ -491,13 +491,16 @@ extern "C" rr_status rr_create_operator(const rr_grid* g, const rr_baseflow* fl,
                                         const double* weights, int device, rr_operator** out) {
   if (!g || !fl || !out) return arg_error("rr_create_operator: null argument");
   *out = nullptr;
-  if (g->kind != RR_ADVDIFF_SCALAR && g->kind != RR_ISO_NS2D)
+  if (g->kind != RR_ADVDIFF_SCALAR && g->kind != RR_ISO_NS2D && g->kind != RR_ISO_NS2D_KZ)
     return arg_error("rr_create_operator: unknown operator kind");
+  const bool ns = g->kind != RR_ADVDIFF_SCALAR;
+  if (g->kind == RR_ISO_NS2D_KZ && !std::isfinite(g->kz))
+    return arg_error("rr_create_operator: kz must be finite");
   if (g->nx < 3 || g->ny < 3) return arg_error("rr_create_operator: nx and ny must be >= 3");
   const int q = g->kind;
   if (q * g->ny > 1024) return arg_error("rr_create_operator: block size q*ny must be <= 1024");
   if (!(g->re > 0)) return arg_error("rr_create_operator: re must be positive");
-  if (g->kind == RR_ISO_NS2D && !(g->mach > 0))
+  if (ns && !(g->mach > 0))
     return arg_error("rr_create_operator: mach must be positive");
   if (!(g->x1 > g->x0) || !(g->y1 > g->y0)) return arg_error("rr_create_operator: empty domain");
   if (g->sponge_max != 0.0 && !(g->sponge_frac > 0.0 && g->sponge_frac <= 0.5))
@@ -507,7 +510,7 @@ extern "C" rr_status rr_create_operator(const rr_grid* g, const rr_baseflow* fl,
       return arg_error("rr_create_operator: neumann masks must be bit masks over the q variables");
   if (g->periodic_y && (g->neumann[2] || g->neumann[3]))
     return arg_error("rr_create_operator: a periodic y direction has no y boundary closure");
-  if (!fl->u || !fl->v || (g->kind == RR_ISO_NS2D && !fl->rho))
+  if (!fl->u || !fl->v || (ns && !fl->rho))
     return arg_error("rr_create_operator: missing base-flow field");
   const size_t npts = (size_t)g->nx * g->ny;
   const size_t N = npts * q;
@@ -548,7 +551,7 @@ extern "C" rr_status rr_create_operator(const rr_grid* g, const rr_baseflow* fl,
   if (fl->rho) std::memcpy(hf.data(), fl->rho, npts * sizeof(double));
   std::memcpy(hf.data() + npts, fl->u, npts * sizeof(double));
   std::memcpy(hf.data() + 2 * npts, fl->v, npts * sizeof(double));
-  if (g->kind == RR_ISO_NS2D)
+  if (ns)
     for (size_t p = 0; p < npts; ++p)
       if (!(hf[p] > 0.0)) return fail(arg_error("rr_create_operator: rho must be positive"));
   cudaError_t e = cudaMemcpy(d.flow, hf.data(), hf.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -610,9 +613,27 @@ extern "C" rr_status rr_apply(rr_operator* op, int nshift, const double* shifts,
   if (s != RR_OK) return s;
   cudaError_t e = cudaMemcpyAsync(sd, shifts, nshift * sizeof(double2), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) { cudaFree(sd); return cuda_status(e, "rr_apply shifts"); }
-  s = launch_apply(op->d, nshift, sd, k, adjoint, (const double2*)x, (double2*)y, st);
+  // bi-global operators: y = D (s I - L~) D^{-1} x with the real L~ = D^{-1} L D
+  // (the adjoint likewise, D unitary); D^{-1} x goes through a temporary
+  double2* xt = nullptr;
+  const double2* xin = (const double2*)x;
+  if (op->d.q == 4) {
+    const size_t bytes = (size_t)nshift * op->d.n * k * sizeof(double2);
+    s = dalloc(&xt, bytes);
+    if (s == RR_OK) e = cudaMemcpyAsync(xt, x, bytes, cudaMemcpyDeviceToDevice, st);
+    if (s == RR_OK && e == cudaSuccess) s = launch_kz_phase(nshift, op->d.n, k, 4, -1, xt, st);
+    if (s != RR_OK || e != cudaSuccess) {
+      cudaFree(sd);
+      cudaFree(xt);
+      return s != RR_OK ? s : cuda_status(e, "rr_apply");
+    }
+    xin = xt;
+  }
+  s = launch_apply(op->d, nshift, sd, k, adjoint, xin, (double2*)y, st);
+  if (s == RR_OK) s = launch_kz_phase(nshift, op->d.n, k, op->d.q, 1, (double2*)y, st);
   e = cudaStreamSynchronize(st);
   cudaFree(sd);
+  cudaFree(xt);
   if (s != RR_OK) return s;
   if (e != cudaSuccess) return cuda_status(e, "rr_apply");
   return RR_OK;
@@ -878,11 +899,14 @@ extern "C" rr_status rr_solve(rr_factors* fa, int k, int adjoint, const void* b,
   const size_t bytes = (size_t)F * d.n * k * sizeof(double2);
   cudaStream_t st = fa->stream;
   // R b = W^{1/2} A^{-1} W^{-1/2} b ;  R^H b = W^{-1/2} A^{-H} W^{1/2} b
+  // (bi-global operators: the solve runs on D^{-1} L D, D = diag(1, 1, 1, i))
   RR_CUDA(cudaMemcpyAsync(w.W2, b, bytes, cudaMemcpyDeviceToDevice, st));
+  if ((s = launch_kz_phase(F, d.n, k, d.q, -1, w.W2, st)) != RR_OK) return s;
   if ((s = launch_scale_rows(F, d.n, k, adjoint ? d.wsqrt : d.wisqrt, w.W2, st)) != RR_OK) return s;
   s = solve_refined(fa, k, adjoint, w.W2, (double2*)x, refine_tol, max_refine, w, info);
   if (s != RR_OK && s != RR_ERR_NOCONV) return s;
   rr_status s2 = launch_scale_rows(F, d.n, k, adjoint ? d.wisqrt : d.wsqrt, (double2*)x, st);
+  if (s2 == RR_OK) s2 = launch_kz_phase(F, d.n, k, d.q, 1, (double2*)x, st);
   if (s2 != RR_OK) return s2;
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e, "rr_solve");
@@ -937,6 +961,9 @@ extern "C" rr_status rr_sketch_ex(rr_factors* fa, int k, const uint64_t* seeds, 
     if ((s = launch_philox(F, N, k, w.seeds, phi, d.wisqrt, w.W1, st, kind, dens)) != RR_OK)
       return s;
   }
+  // (bi-global operators: everything below runs on D^{-1} L D, so Omega
+  // enters as D^{-1} Omega and V leaves as D V)
+  if ((s = launch_kz_phase(F, N, k, d.q, -1, w.W1, st)) != RR_OK) return s;
   // Y = W^{1/2} A^{-1} Omega'  (second step)
   if ((s = note(solve_refined(fa, k, 0, w.W1, w.W2, refine_tol, max_refine, w, info))) != RR_OK)
     return s;
@@ -970,6 +997,7 @@ extern "C" rr_status rr_sketch_ex(rr_factors* fa, int k, const uint64_t* seeds, 
   if ((s = launch_jacobi_svd(F, k, w.R2i, w.sig, w.Ul, w.Vr, w.sweeps, st)) != RR_OK) return s;
   if ((s = launch_small_mul(F, k, w.Rd, w.Ul, w.R1, st)) != RR_OK) return s;
   if ((s = launch_right_mul(F, N, k, w.W3, w.R1, (double2*)V, st)) != RR_OK) return s;
+  if ((s = launch_kz_phase(F, N, k, d.q, 1, (double2*)V, st)) != RR_OK) return s;
   RR_CUDA(cudaMemcpyAsync(sigma_halko, w.sig, (size_t)F * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (fa->sched_mode != SCHED_REPLAY) RR_CUDA(cudaStreamSynchronize(st));
   return conv;
@@ -998,11 +1026,14 @@ extern "C" rr_status rr_modes(rr_factors* fa, int k, void* V, void* U, double* s
   cudaStream_t st = fa->stream;
   rr_status conv = RR_OK;
   // U Sigma = W^{1/2} A^{-1} W^{-1/2} V  (Eq. 8)
+  // (bi-global operators: the solve runs on D^{-1} L D, D = diag(1, 1, 1, i))
   RR_CUDA(cudaMemcpyAsync(w.W1, V, bytes, cudaMemcpyDeviceToDevice, st));
+  if ((s = launch_kz_phase(F, N, k, d.q, -1, w.W1, st)) != RR_OK) return s;
   if ((s = launch_scale_rows(F, N, k, d.wisqrt, w.W1, st)) != RR_OK) return s;
   s = solve_refined(fa, k, 0, w.W1, w.W2, refine_tol, max_refine, w, info);
   if (s == RR_ERR_NOCONV) conv = s; else if (s != RR_OK) return s;
   if ((s = launch_scale_rows(F, N, k, d.wsqrt, w.W2, st)) != RR_OK) return s;
+  if ((s = launch_kz_phase(F, N, k, d.q, 1, w.W2, st)) != RR_OK) return s;
   if (!orthogonalize) {
     // sigma_j = ||(U Sigma)_j||, u_j = (U Sigma)_j / sigma_j
     if ((s = launch_colnorm2(F, N, k, w.W2, w.dpart, w.nblk_col, sigma, st)) != RR_OK) return s;
@@ -1030,6 +1061,10 @@ extern "C" rr_status rr_gain_grad(rr_factors* fa, int k, int J, const void* U, c
   if (!U || !V || !sigma || !grad) return arg_error("rr_gain_grad: null argument");
   if (J < 1 || J > k) return arg_error("rr_gain_grad: J must be in [1, k]");
   if (max_refine < 0) return arg_error("rr_gain_grad: max_refine must be >= 0");
+  if (fa->op->d.q == 4) {
+    g_err = "rr_gain_grad: not implemented for the bi-global operator";
+    return RR_ERR_UNSUPPORTED;
+  }
   DeviceGuard guard(fa->op->d.device);
   info_reset(info);
   Work w;

@@ -241,6 +241,9 @@ rr_status launch_philox(int F, int N, int k, const uint64_t* seeds_dev, const do
                         const double* wisqrt, double2* out, cudaStream_t st, int kind = 0,
                         double density = 1.0);
 rr_status launch_scale_rows(int F, int N, int k, const double* w, double2* x, cudaStream_t st);
+// bi-global operators (q = 4): x <- D x (sign > 0) or D^{-1} x, D = diag(1, 1, 1, i)
+// per point; no-op for q != 4
+rr_status launch_kz_phase(int F, int N, int k, int q, int sign, double2* x, cudaStream_t st);
 rr_status launch_convert_d2f(size_t n, const double2* in, float2* out, cudaStream_t st);
 rr_status launch_convert_f2d(size_t n, const float2* in, double2* out, int accumulate,
                              cudaStream_t st);

@@ -21,6 +21,7 @@ import numpy as np
 
 KIND_ADVDIFF = 1  # scalar linearised advection-diffusion, q = 1
 KIND_NS2D = 3     # isothermal compressible Navier-Stokes (rho, u, v), q = 3
+KIND_NS2D_KZ = 4  # bi-global: (rho, u, v, w) ~ exp(i kz z) about a z-invariant flow, q = 4
 
 
 @dataclasses.dataclass(frozen=True)
@@ -41,10 +42,12 @@ class Grid:
     # variables whose ghost node equals the adjacent interior node (Neumann);
     # clear bits keep the zero (Dirichlet) ghost
     neumann: tuple = (0, 0, 0, 0)
+    # spanwise wavenumber of the bi-global operator (KIND_NS2D_KZ)
+    kz: float = 0.0
 
     @property
     def q(self) -> int:
-        return 1 if self.kind == KIND_ADVDIFF else 3
+        return {KIND_ADVDIFF: 1, KIND_NS2D_KZ: 4}.get(self.kind, 3)
 
     @property
     def b(self) -> int:
@@ -163,6 +166,15 @@ def ns_grid(nx: int, ny: int, re: float = 500.0, mach: float = 0.3,
     return Grid(kind=KIND_NS2D, nx=nx, ny=ny, x0=0.0, x1=20.0, y0=-5.0,
                 y1=5.0, re=re, mach=mach, sponge_max=1.0, sponge_frac=0.1,
                 neumann=tuple(neumann))
+
+
+def kz_grid(nx: int, ny: int, kz: float, re: float = 500.0, mach: float = 0.3,
+            neumann: tuple = (0, 0, 0, 0)) -> Grid:
+    """The bi-global operator (rho, u, v, w) at spanwise wavenumber kz on the
+    same domain and sponge as ns_grid (Sec. III.A/B: k_z L_c in {0, 20 pi})."""
+    return Grid(kind=KIND_NS2D_KZ, nx=nx, ny=ny, x0=0.0, x1=20.0, y0=-5.0,
+                y1=5.0, re=re, mach=mach, sponge_max=1.0, sponge_frac=0.1,
+                neumann=tuple(neumann), kz=float(kz))
 
 
 def config_tiny() -> Workload:
