@@ -93,7 +93,7 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
                  float2* __restrict__ Bin_all, int* __restrict__ flag) {
   constexpr int NB = GW_NB;
   constexpr int MAXW = GW_PANEL_THREADS / 32;
-  __shared__ float2 cand[2][MAXW][NB];
+  __shared__ __align__(16) float2 cand[2][MAXW][NB];
   __shared__ float candv[2][MAXW];
   __shared__ int candi[2][MAXW];
   __shared__ int piv_sm[NB];
@@ -139,43 +139,56 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
       if (a1 && v1 > bv) { bv = v1; bi = r1; }
     }
     const int mine = bi;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
-    }
+    // warp argmax in two warp reductions: the largest key (the bits of a
+    // non-negative float order like the float; ineligible rows key 0), then
+    // the lowest row holding it
+    const unsigned key = bv >= 0.f ? __float_as_uint(bv) + 1u : 0u;
+    const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+    bi = (int)__reduce_min_sync(0xffffffffu, key == kmax ? (unsigned)bi : 0x7fffffffu);
+    bv = kmax == 0u ? -1.f : __uint_as_float(kmax - 1u);
     if (bi == mine && bi != 0x7fffffff) {
+      // 16-byte stores: the shared-memory pipe is the step's bottleneck
+      float4* dst = reinterpret_cast<float4*>(cand[buf][warp]);
       if (RPT == 2 && bi == r1) {
 #pragma unroll
-        for (int c = 0; c < NB; ++c) cand[buf][warp][c] = x1[c];
+        for (int c = 0; c < NB; c += 2) dst[c / 2] = make_float4(x1[c].x, x1[c].y, x1[c + 1].x, x1[c + 1].y);
       } else {
 #pragma unroll
-        for (int c = 0; c < NB; ++c) cand[buf][warp][c] = x0[c];
+        for (int c = 0; c < NB; c += 2) dst[c / 2] = make_float4(x0[c].x, x0[c].y, x0[c + 1].x, x0[c + 1].y);
       }
       candv[buf][warp] = bv;
       candi[buf][warp] = bi;
     }
     __syncthreads();
-    float pv = lane < nw ? candv[buf][lane] : -2.f;
-    int pi = lane < nw ? candi[buf][lane] : 0x7fffffff;
-    int pw = lane;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float v2 = __shfl_xor_sync(0xffffffffu, pv, o);
-      const int i2 = __shfl_xor_sync(0xffffffffu, pi, o);
-      const int w2 = __shfl_xor_sync(0xffffffffu, pw, o);
-      if (v2 > pv || (v2 == pv && i2 < pi)) { pv = v2; pi = i2; pw = w2; }
-    }
+    // every warp reduces the per-warp candidates the same way; the winning
+    // warp is the lowest lane holding the winner
+    const float cv = lane < nw ? candv[buf][lane] : -2.f;
+    const unsigned ck = cv >= 0.f ? __float_as_uint(cv) + 1u : 0u;
+    const unsigned cmax = __reduce_max_sync(0xffffffffu, ck);
+    const unsigned ci = lane < nw ? (unsigned)candi[buf][lane] : 0x7fffffffu;
+    const int pi = (int)__reduce_min_sync(0xffffffffu, ck == cmax ? ci : 0x7fffffffu);
+    const int pw = __ffs(__ballot_sync(0xffffffffu, ck == cmax && ci == (unsigned)pi)) - 1;
+    const float pv = cmax == 0u ? -1.f : __uint_as_float(cmax - 1u);
     if (t == 0) {
       piv_sm[j] = pi;
       if (!(pv > 0.f)) flag[f] = 1;
     }
-    const float2* prow = cand[buf][pw];
+    // the pivot row in registers (16-byte loads, broadcast to the warp)
+    float2 prow[NB];
+    {
+      const float4* src = reinterpret_cast<const float4*>(cand[buf][pw]);
+#pragma unroll
+      for (int c = 0; c < NB; c += 2) {
+        const float4 v = src[c / 2];
+        prow[c] = make_float2(v.x, v.y);
+        prow[c + 1] = make_float2(v.z, v.w);
+      }
+    }
     float2 piv = prow[0];
     if (piv.x * piv.x + piv.y * piv.y == 0.f) piv = make_float2(1e-18f, 0.f);
     const float pd = piv.x * piv.x + piv.y * piv.y;
-    const float2 pinv = make_float2(piv.x / pd, -piv.y / pd);
+    const float ipd = __frcp_rn(pd);
+    const float2 pinv = make_float2(piv.x * ipd, -piv.y * ipd);
     // every held row: x -= (x_0 / pivot) * pivot row, x_0 <- -x_0 / pivot;
     // the pivot row itself is scaled by 1/pivot, its x_0 <- 1/pivot
     const bool p0 = r0 == pi, p1 = RPT == 2 && r1 == pi;
@@ -245,6 +258,81 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
     float2 v = make_float2(0.f, 0.f);
     if (c < nbk && !(m >= k0 && m < k0 + nbk)) v = M[(size_t)piv_sm[c] * b + m];
     Bin[(size_t)c * b + m] = v;
+  }
+}
+
+// ------------------------------------------------------------ inner update
+// The transformations of panel K = [k0, k0 + 16) applied to the rest of its
+// slab, on the FP32 CUDA cores (a rank-16 contraction is bound by moving the
+// slab, not by its flops):
+//   M[r, m] += M[r, K] Bin[:, m]      rows r not pivoted in K,
+//   M[r, m]  = M[r, K] Bin[:, m]      the pivot rows of K (T^{-1} B itself),
+// for the slab columns m outside K.  CTA = (64-row tile, problem); the tile's
+// multipliers M[rows, K] and all of Bin's slab columns sit in shared memory;
+// thread (ty, tx) accumulates rows ty + 16 i (i < 4) x slab columns tx + 16 j
+// (j < 8) in registers, so each shared-memory load feeds 4 or 8 complex FMAs.
+constexpr int IU_RT = 64, IU_THREADS = 256;
+
+__global__ void __launch_bounds__(IU_THREADS)
+gjw_inner_update_kernel(int b, int k0, int c0, int c1, float2* __restrict__ Mall,
+                        const float2* __restrict__ Bin_all, const int* __restrict__ rowpiv_all) {
+  constexpr int NB = GW_NB, RI = IU_RT / 16, CJ = GW_W / 16;
+  __shared__ __align__(16) float2 As[IU_RT][NB + 1];
+  __shared__ __align__(16) float2 Bs[NB][GW_W];
+  const int f = blockIdx.y, r0 = blockIdx.x * IU_RT;
+  const int w = c1 - c0;
+  float2* M = Mall + (size_t)f * b * b;
+  const float2* Bin = Bin_all + (size_t)f * GW_BIN_ROWS * b;
+  // the accumulators start from the old values (zero on pivot rows), loaded
+  // first so that their latency overlaps the staging and the contraction
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int* rowpiv = rowpiv_all + (size_t)f * b;
+  float2 acc[RI][CJ];
+  unsigned upd[RI];
+#pragma unroll
+  for (int i = 0; i < RI; ++i) {
+    const int r = r0 + ty + 16 * i;
+    const int rp = r < b ? rowpiv[r] : -1;
+    const bool pivot = rp >= k0 && rp < k0 + NB;
+    const float2* Mr = M + (size_t)(r < b ? r : 0) * b + c0;
+    upd[i] = 0u;
+#pragma unroll
+    for (int j = 0; j < CJ; ++j) {
+      const int m = tx + 16 * j;
+      const bool u = r < b && m < w && !(c0 + m >= k0 && c0 + m < k0 + NB);
+      upd[i] |= u ? (1u << j) : 0u;
+      acc[i][j] = (u && !pivot) ? Mr[m] : make_float2(0.f, 0.f);
+    }
+  }
+  for (int e = threadIdx.x; e < IU_RT * NB; e += IU_THREADS) {
+    const int rr = e / NB, k = e - rr * NB, r = r0 + rr;
+    As[rr][k] = (r < b && k0 + k < b) ? M[(size_t)r * b + k0 + k] : make_float2(0.f, 0.f);
+  }
+  for (int e = threadIdx.x; e < NB * GW_W; e += IU_THREADS) {
+    const int k = e / GW_W, m = e - k * GW_W;
+    Bs[k][m] = m < w ? Bin[(size_t)k * b + c0 + m] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int k = 0; k < NB; ++k) {
+    float2 a[RI], bk[CJ];
+#pragma unroll
+    for (int i = 0; i < RI; ++i) a[i] = As[ty + 16 * i][k];
+#pragma unroll
+    for (int j = 0; j < CJ; ++j) bk[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+      for (int j = 0; j < CJ; ++j) acc[i][j] = cfma(a[i], bk[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < RI; ++i) {
+    const int r = r0 + ty + 16 * i;
+    if (r >= b) continue;
+    float2* Mr = M + (size_t)r * b + c0;
+#pragma unroll
+    for (int j = 0; j < CJ; ++j)
+      if (upd[i] & (1u << j)) Mr[tx + 16 * j] = acc[i][j];
   }
 }
 
@@ -721,12 +809,13 @@ rr_status factor_wide_impl(rr_factors* fa) {
                                                     fa->pivslot,
                                                     reinterpret_cast<float2*>(fa->Bbuf), fa->flag);
         prof_end(PROF_PANEL, sx);
-        // the rest of the slab: its column tiles (the panel's own columns get
-        // zero from Bin)
+        // the rest of the slab (exact FP32 on the CUDA cores)
         if (c1 - c0 > nbk) {
-          const int t0 = c0 / GG_CT, t1 = (c1 + GG_CT - 1) / GG_CT;
-          rr_status r = launch_gemm<SPLIT>(fa, tA, tBin, k0, GW_NB, t0, t1, 0, 0, sx);
-          if (r != RR_OK) return r;
+          prof_begin(PROF_UPDATE, sx);
+          gjw_inner_update_kernel<<<dim3((b + IU_RT - 1) / IU_RT, F), IU_THREADS, 0, sx>>>(
+              b, k0, c0, c1, M, reinterpret_cast<const float2*>(fa->Bbuf), fa->rowpiv);
+          prof_end(PROF_UPDATE, sx);
+          RR_CUDA(cudaGetLastError());
         }
       }
       return RR_OK;
