@@ -477,8 +477,8 @@ __device__ __forceinline__ bool tc_poll(uint64_t* bar, uint32_t parity, uint32_t
   return tc::mbar_wait(bar, parity, tries);
 }
 
-constexpr int TC2_CONV = 256;                 // converter threads (warps 0-7)
-constexpr int TC2_THREADS = TC2_CONV + 32;    // + control warp 8 (TMA producer, MMA issuer)
+constexpr int TC2_CONV = 512;                 // converter threads (warps 0-15)
+constexpr int TC2_THREADS = TC2_CONV + 32;    // + control warp 16 (TMA producer, MMA issuer)
 
 template <bool TRANS, int SPLIT>
 __global__ void __launch_bounds__(TC2_THREADS, 1)
@@ -620,16 +620,18 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
             }
             tc::store_split<SPLIT>(gv, ap, tc::kmajor_off32<SPLIT>(r, 4 * p));
           }
+          // B~ rows 2j (x_r, -x_i) and 2j + 1 (x_i, x_r) of column j: consecutive
+          // threads take consecutive rows, so each 8-thread phase of the
+          // 16-byte stores covers the eight row slots of a core matrix
           const int m0 = (ks * cpp + lc) * TC2_KC;
-          for (int it = tid; it < kp * 8; it += TC2_CONV) {
-            const int j = it % kp, p = it / kp;
+          for (int it = tid; it < 2 * kp * 8; it += TC2_CONV) {
+            const int row = it % (2 * kp), p = it / (2 * kp), j = row >> 1;
             const int ma = m0 + 2 * p, mb = ma + 1;
             const float2 t0 = (j < k && ma < b) ? Rt[(2 * p) * k + j] : make_float2(0.f, 0.f);
             const float2 t1 = (j < k && mb < b) ? Rt[(2 * p + 1) * k + j] : make_float2(0.f, 0.f);
-            tc::store_split<SPLIT>(make_float4(t0.x, -t0.y, t1.x, -t1.y), bp,
-                                   tc::kmajor_off32<SPLIT>(2 * j, 4 * p));
-            tc::store_split<SPLIT>(make_float4(t0.y, t0.x, t1.y, t1.x), bp,
-                                   tc::kmajor_off32<SPLIT>(2 * j + 1, 4 * p));
+            const float4 v = (row & 1) ? make_float4(t0.y, t0.x, t1.y, t1.x)
+                                       : make_float4(t0.x, -t0.y, t1.x, -t1.y);
+            tc::store_split<SPLIT>(v, bp, tc::kmajor_off32<SPLIT>(row, 4 * p));
           }
         }
         tc::fence_async_smem();
@@ -664,27 +666,38 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
     failed = __syncthreads_or(ok ? 0 : 1) != 0;
     if (failed) break;
     tc::fence_after_sync();
-    if (warp < 4) {
-      const int r = rt * TC_RT + warp * 32 + lane;
+    if (tid < TC2_CONV) {
+      // 16x256b fragments: warp w reads lanes 32 (w % 4) + 16 sb + [0, 16)
+      // (sb = (w / 4) & 1) and float columns 32 hh + [0, 32) (hh = w / 8) of
+      // each partial product; thread t holds rows t/4 and t/4 + 8 and complex
+      // columns 4 r + t % 4, so four consecutive threads write 32 contiguous
+      // bytes of a row (whole sectors)
+      const int lq = warp & 3, sb = (warp >> 2) & 1;
       float2* pf = part + ((size_t)ks * F + f) * (size_t)b * k;
-      for (int cc = 0; cc < N / 16; ++cc) {
+      for (int hh = warp >> 3; hh < (N + 31) / 32; hh += 2) {
         float v[16], w[16];
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 16);
-        tc::tmem_ld16(ta, v);
+        const uint32_t ta =
+            tmem + ((uint32_t)(lq * 32 + 16 * sb) << 16) + (uint32_t)(hh * 32);
+        tc::tmem_ld_16x256b_x4(ta, v);
 #pragma unroll
         for (int a = 1; a < 6; ++a) {  // the six partial products
           // x3: sets 0/1 x {hi.hi, hi.lo, lo.hi}; x6: p0.q0..2, p1.q0..1, p2.q0
           const uint32_t col = X6 ? (uint32_t)(a * N)
                                   : (uint32_t)(a / 3) * set_cols + (uint32_t)(a % 3) * N;
-          tc::tmem_ld16(ta + col, w);
+          tc::tmem_ld_16x256b_x4(ta + col, w);
 #pragma unroll
           for (int tt = 0; tt < 16; ++tt) v[tt] += w[tt];
         }
-        if (r >= b) continue;
 #pragma unroll
-        for (int tt = 0; tt < 8; ++tt) {
-          const int j = cc * 8 + tt;
-          if (j < k) pf[(size_t)r * k + j] = make_float2(v[2 * tt], v[2 * tt + 1]);
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int r = rt * TC_RT + lq * 32 + 16 * sb + (lane >> 2) + 8 * h2;
+          if (r >= b) continue;
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) {
+            const int j = hh * 16 + 4 * rr + (lane & 3);
+            if (j < k)
+              pf[(size_t)r * k + j] = make_float2(v[4 * rr + 2 * h2], v[4 * rr + 2 * h2 + 1]);
+          }
         }
       }
     }
