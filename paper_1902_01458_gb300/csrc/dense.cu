@@ -103,11 +103,33 @@ __global__ void f2d_kernel(size_t n, const float2* __restrict__ in, double2* __r
   }
 }
 
-// Per-column sum of squares, partials over row blocks: part[f][blk][j].
+// The conversions on the problems amap[0..Fa) only: grid (blocks, Fa),
+// a grid-stride loop within problem amap[blockIdx.y].
+__global__ void d2f_map_kernel(size_t nk, const int* __restrict__ amap,
+                               const double2* __restrict__ in, float2* __restrict__ out) {
+  const size_t o = (size_t)amap[blockIdx.y] * nk;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nk;
+       e += (size_t)gridDim.x * blockDim.x)
+    out[o + e] = make_float2((float)in[o + e].x, (float)in[o + e].y);
+}
+
+__global__ void f2d_map_kernel(size_t nk, const int* __restrict__ amap,
+                               const float2* __restrict__ in, double2* __restrict__ out, int acc) {
+  const size_t o = (size_t)amap[blockIdx.y] * nk;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nk;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double2 v = make_double2((double)in[o + e].x, (double)in[o + e].y);
+    if (acc) { v.x += out[o + e].x; v.y += out[o + e].y; }
+    out[o + e] = v;
+  }
+}
+
+// Per-column sum of squares, partials over row blocks: part[slot][blk][j]
+// (slot = blockIdx.y, problem active_problem(amap, slot)).
 __global__ void colnorm2_part_kernel(int N, int k, int nblk, const double2* __restrict__ x,
-                                     double* __restrict__ part) {
+                                     double* __restrict__ part, const int* __restrict__ amap) {
   extern __shared__ double red[];
-  const int f = blockIdx.y, blk = blockIdx.x;
+  const int f = active_problem(amap, blockIdx.y), blk = blockIdx.x;
   const int rows_per = (N + nblk - 1) / nblk;
   const int n0 = blk * rows_per, n1 = min(N, n0 + rows_per);
   const double2* xf = x + (size_t)f * N * k;
@@ -126,18 +148,18 @@ __global__ void colnorm2_part_kernel(int N, int k, int nblk, const double2* __re
   if (threadIdx.x < k) {
     double t = 0.0;
     for (int r = 0; r < lane_rows; ++r) t += red[r * k + threadIdx.x];
-    part[((size_t)f * nblk + blk) * k + threadIdx.x] = t;
+    part[((size_t)blockIdx.y * nblk + blk) * k + threadIdx.x] = t;
   }
 }
 
 __global__ void colnorm2_reduce_kernel(int F, int k, int nblk, const double* __restrict__ part,
-                                       double* __restrict__ out) {
+                                       double* __restrict__ out, const int* __restrict__ amap) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= F * k) return;
-  int f = e / k, j = e % k;
+  int sl = e / k, j = e % k;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[((size_t)f * nblk + b) * k + j];
-  out[e] = sqrt(s);
+  for (int b = 0; b < nblk; ++b) s += part[((size_t)sl * nblk + b) * k + j];
+  out[(size_t)active_problem(amap, sl) * k + j] = sqrt(s);
 }
 
 // Gram partials part[f][blk][a][c] = sum_n conj(Y[n][a]) Y[n][c].
@@ -598,13 +620,34 @@ rr_status launch_convert_f2d(size_t n, const float2* in, double2* out, int acc, 
   return RR_OK;
 }
 
+rr_status launch_convert_d2f_map(int Fa, const int* amap, size_t nk, const double2* in,
+                                 float2* out, cudaStream_t st) {
+  if (Fa <= 0) return RR_OK;
+  prof_count(1);
+  const int bx = (int)std::min<size_t>((nk + 255) / 256, 1024);
+  d2f_map_kernel<<<dim3(bx, Fa), 256, 0, st>>>(nk, amap, in, out);
+  RR_CUDA(cudaGetLastError());
+  return RR_OK;
+}
+
+rr_status launch_convert_f2d_map(int Fa, const int* amap, size_t nk, const float2* in,
+                                 double2* out, int acc, cudaStream_t st) {
+  if (Fa <= 0) return RR_OK;
+  prof_count(1);
+  const int bx = (int)std::min<size_t>((nk + 255) / 256, 1024);
+  f2d_map_kernel<<<dim3(bx, Fa), 256, 0, st>>>(nk, amap, in, out, acc);
+  RR_CUDA(cudaGetLastError());
+  return RR_OK;
+}
+
 rr_status launch_colnorm2(int F, int N, int k, const double2* x, double* part, int nblk,
-                          double* out, cudaStream_t st) {
+                          double* out, cudaStream_t st, const int* amap) {
   int threads = (256 / k) * k;
   prof_count(1);
-  colnorm2_part_kernel<<<dim3(nblk, F), threads, threads * sizeof(double), st>>>(N, k, nblk, x, part);
+  colnorm2_part_kernel<<<dim3(nblk, F), threads, threads * sizeof(double), st>>>(N, k, nblk, x, part,
+                                                                                 amap);
   prof_count(1);
-  colnorm2_reduce_kernel<<<(F * k + 127) / 128, 128, 0, st>>>(F, k, nblk, part, out);
+  colnorm2_reduce_kernel<<<(F * k + 127) / 128, 128, 0, st>>>(F, k, nblk, part, out, amap);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }

@@ -216,8 +216,8 @@ template <bool RESID, int Q>
 __global__ void __launch_bounds__(256)
 apply_adjoint_kernel(OpView op, const double2* __restrict__ shifts, int k,
                      const double2* __restrict__ bvec, const double2* __restrict__ x,
-                     double2* __restrict__ y) {
-  const int f = blockIdx.y;
+                     double2* __restrict__ y, const int* __restrict__ amap) {
+  const int f = amap ? amap[blockIdx.y] : (int)blockIdx.y;
   const int tpr = k < (int)blockDim.x ? k : (int)blockDim.x;
   const int rows_per = blockDim.x / tpr;
   const int rsub = threadIdx.x / tpr, jt = threadIdx.x - rsub * tpr;
@@ -273,8 +273,8 @@ template <bool RESID, int WT>
 __global__ void __launch_bounds__(256)
 apply_ell_kernel(OpView op, const double2* __restrict__ shifts, int k,
                  const double2* __restrict__ bvec, const double2* __restrict__ x,
-                 double2* __restrict__ y) {
-  const int f = blockIdx.y;
+                 double2* __restrict__ y, const int* __restrict__ amap) {
+  const int f = amap ? amap[blockIdx.y] : (int)blockIdx.y;
   const int tpr = k < (int)blockDim.x ? k : (int)blockDim.x;
   const int rows_per = blockDim.x / tpr;
   const int rsub = threadIdx.x / tpr, jt = threadIdx.x - rsub * tpr;
@@ -431,18 +431,19 @@ rr_status build_ell(OpDev& d) {
 // Forward operator application (adjoint == 0) on the ELL copy, by width.
 template <bool RESID>
 static rr_status launch_ell(const OpDev& d, int F, const double2* shifts, int k,
-                            const double2* b, const double2* x, double2* y, cudaStream_t st) {
+                            const double2* b, const double2* x, double2* y, cudaStream_t st,
+                            const int* amap) {
   const dim3 grid = apply_grid(d, F, k);
   const OpView v = view(d);
   switch (d.ell_w) {
-    case 4: apply_ell_kernel<RESID, 4><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
-    case 6: apply_ell_kernel<RESID, 6><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
-    case 8: apply_ell_kernel<RESID, 8><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
-    case 10: apply_ell_kernel<RESID, 10><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
-    case 13: apply_ell_kernel<RESID, 13><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
-    case 16: apply_ell_kernel<RESID, 16><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
-    case 20: apply_ell_kernel<RESID, 20><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
-    case 27: apply_ell_kernel<RESID, 27><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y); break;
+    case 4: apply_ell_kernel<RESID, 4><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y, amap); break;
+    case 6: apply_ell_kernel<RESID, 6><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y, amap); break;
+    case 8: apply_ell_kernel<RESID, 8><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y, amap); break;
+    case 10: apply_ell_kernel<RESID, 10><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y, amap); break;
+    case 13: apply_ell_kernel<RESID, 13><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y, amap); break;
+    case 16: apply_ell_kernel<RESID, 16><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y, amap); break;
+    case 20: apply_ell_kernel<RESID, 20><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y, amap); break;
+    case 27: apply_ell_kernel<RESID, 27><<<grid, 256, 0, st>>>(v, shifts, k, b, x, y, amap); break;
     default: set_error("ELL width without a compiled kernel"); return RR_ERR_ARG;
   }
   RR_CUDA(cudaGetLastError());
@@ -483,16 +484,16 @@ static dim3 apply_grid(const OpDev& d, int F, int k) {
 rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
                        const double2* x, double2* y, cudaStream_t st) {
   prof_count(1);
-  if (!adjoint) return launch_ell<false>(d, F, shifts, k, nullptr, x, y, st);
+  if (!adjoint) return launch_ell<false>(d, F, shifts, k, nullptr, x, y, st, nullptr);
   if (d.q == 4)
     apply_adjoint_kernel<false, 4><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k,
-                                                                        nullptr, x, y);
+                                                                        nullptr, x, y, nullptr);
   else if (d.q == 3)
     apply_adjoint_kernel<false, 3><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k,
-                                                                        nullptr, x, y);
+                                                                        nullptr, x, y, nullptr);
   else
     apply_adjoint_kernel<false, 1><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k,
-                                                                        nullptr, x, y);
+                                                                        nullptr, x, y, nullptr);
   RR_CUDA(cudaGetLastError());
   return RR_OK;
 }
@@ -587,22 +588,23 @@ extern "C" rr_status rr_apply_static(rr_operator* op, int nshift, const double* 
 }
 
 rr_status launch_residual(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
-                          const double2* b, const double2* x, double2* r, cudaStream_t st) {
+                          const double2* b, const double2* x, double2* r, cudaStream_t st,
+                          const int* amap) {
   prof_begin(PROF_RESIDUAL, st);
   if (!adjoint) {
-    rr_status s = launch_ell<true>(d, F, shifts, k, b, x, r, st);
+    rr_status s = launch_ell<true>(d, F, shifts, k, b, x, r, st, amap);
     prof_end(PROF_RESIDUAL, st);
     return s;
   }
   if (d.q == 4)
     apply_adjoint_kernel<true, 4><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, b, x,
-                                                                       r);
+                                                                       r, amap);
   else if (d.q == 3)
     apply_adjoint_kernel<true, 3><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, b, x,
-                                                                       r);
+                                                                       r, amap);
   else
     apply_adjoint_kernel<true, 1><<<apply_grid(d, F, k), 256, 0, st>>>(view(d), shifts, k, b, x,
-                                                                       r);
+                                                                       r, amap);
   prof_end(PROF_RESIDUAL, st);
   RR_CUDA(cudaGetLastError());
   return RR_OK;

@@ -238,13 +238,35 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
   if (fa->sched_mode == SCHED_RECORD) fa->chk_need += 2 * (size_t)F * k * sizeof(double);
   std::vector<double> bn((size_t)F * k), rn((size_t)F * k);
   RR_CUDA(cudaMemcpyAsync(bn.data(), w.bn, bn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // Eager solves on the split tensor-core sweep refine each problem on its
+  // own: a problem leaves the active set once its residual meets tol or a
+  // correction no longer halves it, and the corrections and residuals that
+  // follow run on the active problems only.  Elsewhere (and when recording a
+  // schedule) all problems take every correction until the largest residual
+  // meets tol or stops halving.
+  const bool per_problem = fa->sched_mode == SCHED_EAGER && lo && sweep_tc2_ok(fa, k);
+  struct MapReset {  // the solve path never keeps a subset past this call
+    rr_factors* fa;
+    ~MapReset() {
+      fa->amap = nullptr;
+      fa->Fa = 0;
+    }
+  } map_reset{fa};
+  std::vector<double> relf(F, 0.0), prevf(F, INFINITY);
+  std::vector<char> active(F, 1);
+  std::vector<int> act;  // active problems of the last correction
+  bool subset = false;   // residuals on the list in amap_buf
   int it = 0;
   double rel = 0.0, prev = INFINITY;
   int stagnated = 0;
   rr_status result = RR_OK;
   for (;;) {
-    if ((s = launch_residual(d, F, fa->shifts, k, adjoint, b, x, w.R64, st)) != RR_OK) return s;
-    if ((s = launch_colnorm2(F, d.n, k, w.R64, w.dpart, w.nblk_col, w.rn, st)) != RR_OK) return s;
+    const int* amap = subset ? fa->amap_buf : nullptr;
+    const int nres = subset ? (int)act.size() : F;
+    if ((s = launch_residual(d, nres, fa->shifts, k, adjoint, b, x, w.R64, st, amap)) != RR_OK)
+      return s;
+    if ((s = launch_colnorm2(nres, d.n, k, w.R64, w.dpart, w.nblk_col, w.rn, st, amap)) != RR_OK)
+      return s;
     RR_CUDA(cudaMemcpyAsync(rn.data(), w.rn, rn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     int tc_err = 0;
     RR_CUDA(cudaMemcpyAsync(&tc_err, fa->flag + F, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -257,21 +279,47 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
       return RR_ERR_TIMEOUT;
     }
     rel = 0.0;
-    for (size_t e = 0; e < rn.size(); ++e) {
-      double r = bn[e] > 0.0 ? rn[e] / bn[e] : rn[e];
-      if (!(r == r)) r = INFINITY;
-      rel = std::max(rel, r);
+    for (int f = 0; f < F; ++f) {
+      if (!subset || active[f]) {
+        double rf = 0.0;
+        for (int j = 0; j < k; ++j) {
+          const size_t e = (size_t)f * k + j;
+          double r = bn[e] > 0.0 ? rn[e] / bn[e] : rn[e];
+          if (!(r == r)) r = INFINITY;
+          rf = std::max(rf, r);
+        }
+        relf[f] = rf;
+      }
+      rel = std::max(rel, relf[f]);
     }
     if (it == 0 && info) info->first_residual = std::max(info->first_residual, rel);
-    if (tol <= 0.0 || rel <= tol) break;
+    if (tol <= 0.0) break;
     // The FP64 residual itself carries rounding of order u ||A|| ||x||; once a
     // correction no longer halves the residual, x is as accurate as that
     // floor allows and further sweeps cannot help.
-    if (it > 0 && rel > 0.5 * prev) {
-      stagnated = 1;
-      break;
+    if (per_problem) {
+      act.clear();
+      for (int f = 0; f < F; ++f) {
+        if (!active[f]) continue;
+        if (relf[f] <= tol) {
+          active[f] = 0;
+        } else if (it > 0 && relf[f] > 0.5 * prevf[f]) {
+          active[f] = 0;
+          stagnated = 1;
+        } else {
+          prevf[f] = relf[f];
+          act.push_back(f);
+        }
+      }
+      if (act.empty()) break;
+    } else {
+      if (rel <= tol) break;
+      if (it > 0 && rel > 0.5 * prev) {
+        stagnated = 1;
+        break;
+      }
+      prev = rel;
     }
-    prev = rel;
     if (it >= maxit) {
       char buf[160];
       snprintf(buf, sizeof buf, "refinement stopped after %d iterations at relative residual %.3e > %.3e",
@@ -281,7 +329,23 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
       break;
     }
     // correction d = solve(r); x += d
-    if (!lo) {
+    if (per_problem) {
+      const size_t nk = (size_t)d.n * k;
+      RR_CUDA(cudaMemcpyAsync(fa->amap_buf, act.data(), act.size() * sizeof(int),
+                              cudaMemcpyHostToDevice, st));
+      fa->amap = fa->amap_buf;
+      fa->Fa = (int)act.size();
+      fa->amap_h = act;
+      if ((s = launch_convert_d2f_map(fa->Fa, fa->amap, nk, w.R64, (float2*)w.L1, st)) != RR_OK)
+        return s;
+      if ((s = launch_solve_lo(fa, k, adjoint, w.L1, w.L2, w.L3)) != RR_OK) return s;
+      if ((s = launch_convert_f2d_map(fa->Fa, fa->amap, nk, (const float2*)w.L2, x, 1, st)) !=
+          RR_OK)
+        return s;
+      fa->amap = nullptr;
+      fa->Fa = 0;
+      subset = true;
+    } else if (!lo) {
       // FP64 factors: the correction lands in L2 (complex double here)
       if ((s = launch_solve_lo(fa, k, adjoint, w.R64, w.L2, w.L3)) != RR_OK) return s;
       if ((s = launch_axpy(nel, (const double2*)w.L2, x, st)) != RR_OK) return s;
@@ -691,8 +755,10 @@ extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts
   }
   if ((s = dalloc(&fa->perm, (size_t)nshift * d.b * sizeof(int))) != RR_OK) return fail(s);
   if ((s = dalloc(&fa->ipiv, (size_t)nshift * 32 * sizeof(int))) != RR_OK) return fail(s);
-  // flags: one singular-pivot flag per shift, then the tensor-core wait flag
-  if ((s = dalloc(&fa->flag, (size_t)(nshift + 1) * sizeof(int))) != RR_OK) return fail(s);
+  // flags: one singular-pivot flag per shift, then the tensor-core wait flag,
+  // then room for the active-problem list of the refinement
+  if ((s = dalloc(&fa->flag, (size_t)(2 * nshift + 1) * sizeof(int))) != RR_OK) return fail(s);
+  fa->amap_buf = fa->flag + nshift + 1;
   if ((s = dalloc(&fa->shifts, (size_t)nshift * sizeof(double2))) != RR_OK) return fail(s);
   {
     // the look-ahead panel stream gets the highest priority so its CTAs are
@@ -798,7 +864,8 @@ rr_status factors_view(rr_factors* parent, int f0, int nf, cudaStream_t st, rr_f
     if ((s = dalloc(&v->Pbuf, (size_t)4 * nf * 64 * d.b * sizeof(float2))) != RR_OK) return fail(s);
     v->tma_ok = encode_factor_maps(v);
   }
-  if ((s = dalloc(&v->flag, (size_t)(nf + 1) * sizeof(int))) != RR_OK) return fail(s);
+  if ((s = dalloc(&v->flag, (size_t)(2 * nf + 1) * sizeof(int))) != RR_OK) return fail(s);
+  v->amap_buf = v->flag + nf + 1;
   RR_CUDA(cudaMemsetAsync(v->flag, 0, (nf + 1) * sizeof(int), st));
   v->shifts_h = new double2[nf];
   for (int f = 0; f < nf; ++f) v->shifts_h[f] = parent->shifts_h[f0 + f];

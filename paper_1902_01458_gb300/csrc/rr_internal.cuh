@@ -184,7 +184,19 @@ struct rr_factors {
   int tune_ks;
   int tune_update;
   int factor_cols;
+  // Active problems of the current refinement correction (eager solves on
+  // the tensor-core sweep path): when amap is set, the solve path runs only
+  // the Fa problems amap[0..Fa) (device list in amap_buf, which has room for
+  // F); otherwise all F.
+  int* amap_buf;
+  const int* amap;
+  int Fa;
+  std::vector<int> amap_h;  // host copy of the list
 };
+
+// number of problems the solve path runs on, and the problem of slot s
+inline int active_count(const rr_factors* fa) { return fa->amap ? fa->Fa : fa->F; }
+__device__ __forceinline__ int active_problem(const int* amap, int s) { return amap ? amap[s] : s; }
 
 // Precisions that store complex FP32 factors and run their products on the
 // tensor cores (TF32 or BF16 operand splits).
@@ -211,8 +223,11 @@ rr_status launch_assemble(OpDev& d, const rr_grid& g, cudaStream_t st);
 rr_status build_ell(OpDev& d);
 rr_status launch_apply(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
                        const double2* x, double2* y, cudaStream_t st);
+// r = b - (s I - L) x (or the adjoint); with amap, grid slot f runs problem
+// amap[f] (F slots), else problem f
 rr_status launch_residual(const OpDev& d, int F, const double2* shifts, int k, int adjoint,
-                          const double2* b, const double2* x, double2* r, cudaStream_t st);
+                          const double2* b, const double2* x, double2* r, cudaStream_t st,
+                          const int* amap = nullptr);
 rr_status launch_phi(const OpDev& d, double* phi, cudaStream_t st);
 
 // rr_api.cu: views over factors and graph-mode helpers of batch plans
@@ -234,6 +249,9 @@ rr_status launch_factor_wide(rr_factors* f);
 // sweep.cu: x = A^{-1} b or A^{-H} b with the factors in precision T.
 // b and x are [F][N][k] in the factor precision; tmp same size (adjoint only).
 rr_status launch_solve_lo(rr_factors* f, int k, int adjoint, const void* b, void* x, void* tmp);
+// true when the solves of k columns take the split tensor-core sweep, the
+// one path that can run on a subset of the problems (rr_factors::amap)
+bool sweep_tc2_ok(const rr_factors* f, int k);
 
 // dense.cu
 // kind: 0 Gaussian, 1 Rademacher, 2 sparse Rademacher of the given density
@@ -247,8 +265,15 @@ rr_status launch_kz_phase(int F, int N, int k, int q, int sign, double2* x, cuda
 rr_status launch_convert_d2f(size_t n, const double2* in, float2* out, cudaStream_t st);
 rr_status launch_convert_f2d(size_t n, const float2* in, double2* out, int accumulate,
                              cudaStream_t st);
+// the same on the problems amap[0..Fa) of [F][nk] arrays only
+rr_status launch_convert_d2f_map(int Fa, const int* amap, size_t nk, const double2* in,
+                                 float2* out, cudaStream_t st);
+rr_status launch_convert_f2d_map(int Fa, const int* amap, size_t nk, const float2* in,
+                                 double2* out, int accumulate, cudaStream_t st);
+// column 2-norms out[f][j] of x[f] ([F][N][k]); with amap only the problems
+// amap[0..F) (F slots), the other entries of out untouched
 rr_status launch_colnorm2(int F, int N, int k, const double2* x, double* part, int nblk,
-                          double* out, cudaStream_t st);
+                          double* out, cudaStream_t st, const int* amap = nullptr);
 rr_status launch_gram(int F, int N, int k, const double2* Y, double2* part, int nblk,
                       double2* G, cudaStream_t st);
 rr_status launch_cholesky(int F, int k, const double2* G, double2* R, double2* Rinv,

@@ -34,18 +34,20 @@ __device__ __forceinline__ int slotv(int dx, int dy) { return (dx + 1) * 3 + (dy
 //   FWD     (i > 0)      t = in_i + L_{i,i-1} out_{i-1}
 //   BWD                  t = C_i out_{i+1} = -L_{i,i+1} out_{i+1}
 //   ADJ_BWD (i < nx-1)   t = in_i + L_{i+1,i}^T out_{i+1}
+// Grid (ceil(b k / blockDim), active problems): problem f =
+// active_problem(amap, blockIdx.y), 32-bit indices within the problem.
 template <typename T, int MODE>
 __global__ void sweep_rhs_kernel(OpView op, int i, int k, const C_t<T>* in, const C_t<T>* out,
-                                 C_t<T>* __restrict__ tbuf, size_t tstride, int F) {
+                                 C_t<T>* __restrict__ tbuf, size_t tstride,
+                                 const int* __restrict__ amap) {
   using C = C_t<T>;
   const int b = op.b, q = op.q;
   const size_t NK = (size_t)op.n * k;
-  const size_t total = (size_t)F * b * k;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    int f = (int)(e / ((size_t)b * k));
-    int rem = (int)(e - (size_t)f * b * k);
-    int m = rem / k, j = rem - m * k;
+  const int f = active_problem(amap, blockIdx.y);
+  {
+    const int rem = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rem >= b * k) return;
+    const int m = rem / k, j = rem - m * k;
     const C* outf = out + (size_t)f * NK;
     size_t row = (size_t)i * b + m;
     C v = czero<C>();
@@ -90,18 +92,18 @@ __global__ void sweep_rhs_kernel(OpView op, int i, int k, const C_t<T>* in, cons
 }
 
 // h_{i+1} -= C_i^H t, i.e. h_{i+1}[c] += sum_m L[(i,m),(i+1,c)] t[m] (L real).
+// Grid (ceil(b k / blockDim), F) as sweep_rhs_kernel.
 template <typename T>
 __global__ void adj_couple_kernel(OpView op, int i, int k, const C_t<T>* __restrict__ tbuf,
-                                  size_t tstride, C_t<T>* h, int F) {
+                                  size_t tstride, C_t<T>* h, const int* __restrict__ amap) {
   using C = C_t<T>;
   const int b = op.b, q = op.q;
   const size_t NK = (size_t)op.n * k;
-  const size_t total = (size_t)F * b * k;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    int f = (int)(e / ((size_t)b * k));
-    int rem = (int)(e - (size_t)f * b * k);
-    int c = rem / k, j = rem - c * k;
+  const int f = active_problem(amap, blockIdx.y);
+  {
+    const int rem = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rem >= b * k) return;
+    const int c = rem / k, j = rem - c * k;
     const int iyc = c / q, cc = c - iyc * q;
     const C* tf = tbuf + (size_t)f * tstride;
     size_t idx = (size_t)f * NK + ((size_t)(i + 1) * b + c) * k + j;
@@ -484,7 +486,8 @@ template <bool TRANS, int SPLIT>
 __global__ void __launch_bounds__(TC2_THREADS, 1)
 sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp, int blk,
                  int nx, int nrt, int KS, int cpp, const float2* rhs, size_t rstride,
-                 float2* __restrict__ part, int F, int* err, uint32_t tries, int stall) {
+                 float2* __restrict__ part, int F, int Fa, const int* __restrict__ amap, int* err,
+                 uint32_t tries, int stall) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t full_bar[TC2_STAGES];
   __shared__ uint64_t mma_bar[2];
@@ -502,7 +505,7 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool ctrl = (tid == TC2_CONV);  // the one thread that feeds TMA and the tensor core
   const int nch = (b + TC2_KC - 1) / TC2_KC;
-  const int nitems = nrt * KS * F;
+  const int nitems = nrt * KS * Fa;  // over the active problems
   const int my_items = nitems > (int)blockIdx.x
                            ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
                            : 0;
@@ -519,7 +522,7 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
     const int it = (int)blockIdx.x + t * (int)gridDim.x;
     rt = it % nrt;
     ks = (it / nrt) % KS;
-    f = it / (nrt * KS);
+    f = active_problem(amap, it / (nrt * KS));
   };
   auto item_len = [&](int ks) { return min(nch, ks * cpp + cpp) - ks * cpp; };
 
@@ -720,17 +723,20 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
 }
 
 // Sum the KS partial products in a fixed order and apply the step epilogue.
+// Grid (ceil(b k / blockDim), active problems): problem f =
+// active_problem(amap, blockIdx.y).
 template <int EPI>
 __global__ void sweep_combine_kernel(int F, int b, int k, int KS, size_t NK, int ob,
                                      const float2* __restrict__ part, float2* out, float2* tmp,
-                                     size_t tstride) {
+                                     size_t tstride, const int* __restrict__ amap) {
   const size_t total = (size_t)F * b * k;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
+  const int f = active_problem(amap, blockIdx.y);
+  {
+    const int rem = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rem >= b * k) return;
+    const size_t e = (size_t)f * b * k + rem;
     float2 s = part[e];
     for (int q = 1; q < KS; ++q) s = cadd(s, part[(size_t)q * total + e]);
-    const int f = (int)(e / ((size_t)b * k));
-    const size_t rem = e - (size_t)f * b * k;
     if (EPI == EPI_TMP) {
       tmp[(size_t)f * tstride + rem] = s;
     } else {
@@ -756,9 +762,21 @@ rr_status launch_tc2(const CUtensorMap* tm, int grid_x, int b, int k, int kp, in
   }
   sweep_tc2_kernel<TRANS, SPLIT><<<grid_x, TC2_THREADS, smem, st>>>(
       *tm, b, k, kp, blk, nx, nrt, KS, cpp, reinterpret_cast<const float2*>(rhs), rstride,
-      reinterpret_cast<float2*>(fa->Pbuf), fa->F, fa->flag + fa->F, wait_tries(), take_stall());
+      reinterpret_cast<float2*>(fa->Pbuf), fa->F, active_count(fa), fa->amap, fa->flag + fa->F,
+      wait_tries(), take_stall());
   return RR_OK;
 }
+
+}  // namespace
+
+// The split tensor-core sweep (sweep_tc2_kernel) serves FP32 factors with an
+// even block of at least 128 and an even k of at most 32 columns; only this
+// path runs on a subset of the problems.
+bool sweep_tc2_ok(const rr_factors* fa, int k) {
+  return tc_prec(fa->prec) && k <= 32 && fa->tma_ok && (k % 2) == 0;
+}
+
+namespace {
 
 template <typename T> struct SweepCfg;
 template <> struct SweepCfg<float> { static constexpr int KC = 32, ST = 3; };
@@ -771,11 +789,11 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
   using C = C_t<T>;
   constexpr int KC = SweepCfg<T>::KC, ST = SweepCfg<T>::ST;
   const OpDev& d = fa->op->d;
-  const int b = d.b, F = fa->F;
+  const int b = d.b, F = fa->F, Fa = active_count(fa);
   const size_t NK = (size_t)d.n * k;
   cudaStream_t st = fa->stream;
   if constexpr (std::is_same<T, float>::value) {
-    if (tc_prec(fa->prec) && kp <= 32 && fa->tma_ok && (k % 2) == 0) {
+    if (sweep_tc2_ok(fa, k)) {
       const int nrt = (b + TC_RT - 1) / TC_RT;
       const int nch = (b + TC2_KC - 1) / TC2_KC;
       const int nsm = num_sms(d.device);
@@ -785,7 +803,7 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
       for (int ksc = 1; ksc <= 4 && ksc <= nch; ++ksc) {
         const int cppc = (nch + ksc - 1) / ksc;
         const int ksr = (nch + cppc - 1) / cppc;
-        const long items = (long)nrt * F * ksr;
+        const long items = (long)nrt * Fa * ksr;
         const long waves = (items + nsm - 1) / nsm;
         const double eff = (double)items / (double)(waves * nsm);
         if (eff > best + 1e-9) { best = eff; KS = ksr; }
@@ -795,7 +813,7 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
         KS = (nch + cppc - 1) / cppc;
       }
       const int cpp = (nch + KS - 1) / KS;
-      const int nitems = nrt * F * KS;
+      const int nitems = nrt * Fa * KS;
       const int grid_x = std::min(nitems, nsm);
       const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(fa->tmap[TRANS ? 1 : 0]);
       prof_begin(PROF_SWEEP, st);
@@ -814,14 +832,18 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
                                                   rhs, rstride, fa, st);
       }
       if (ls != RR_OK) return ls;
-      const size_t total = (size_t)F * b * k;
-      const int cblocks = (int)std::min<size_t>((total + 255) / 256, 8192);
-      sweep_combine_kernel<EPI><<<cblocks, 256, 0, st>>>(
-          F, b, k, KS, NK, ob, reinterpret_cast<const float2*>(fa->Pbuf), out, tmp, tstride);
+      const dim3 cgrid((b * k + 255) / 256, Fa);
+      sweep_combine_kernel<EPI><<<cgrid, 256, 0, st>>>(
+          F, b, k, KS, NK, ob, reinterpret_cast<const float2*>(fa->Pbuf), out, tmp, tstride,
+          fa->amap);
       prof_end(PROF_SWEEP, st);
       prof_count(1);
       RR_CUDA(cudaGetLastError());
       return RR_OK;
+    }
+    if (fa->amap) {  // the active-problem list exists only on the split sweep path
+      set_error("sweep: active-problem list on a path without it");
+      return RR_ERR_ARG;
     }
     if (tc_prec(fa->prec) && kp <= 32) {
       const size_t smem = tc_smem_bytes(kp, TRANS) + 1024;
@@ -871,11 +893,10 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
 template <typename T, int MODE>
 void stage_rhs(rr_factors* fa, int i, int k, const C_t<T>* in, const C_t<T>* out, C_t<T>* tb) {
   const OpDev& d = fa->op->d;
-  const size_t total = (size_t)fa->F * d.b * k;
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, 8192);
+  const dim3 grid((d.b * k + 255) / 256, active_count(fa));
   prof_count(1);
-  sweep_rhs_kernel<T, MODE><<<blocks, 256, 0, fa->stream>>>(view(d), i, k, in, out, tb,
-                                                            (size_t)d.b * k, fa->F);
+  sweep_rhs_kernel<T, MODE><<<grid, 256, 0, fa->stream>>>(view(d), i, k, in, out, tb,
+                                                          (size_t)d.b * k, fa->amap);
 }
 
 template <typename T>
@@ -917,17 +938,24 @@ rr_status solve_impl(rr_factors* fa, int k, int adjoint, const void* bv, void* x
     }
   } else {
     C* h = reinterpret_cast<C*>(tmpv);
-    RR_CUDA(cudaMemcpyAsync(h, bin, (size_t)F * NK * sizeof(C), cudaMemcpyDeviceToDevice,
-                            fa->stream));
-    const size_t total = (size_t)F * b * k;
-    const int blocks = (int)std::min<size_t>((total + 255) / 256, 8192);
+    if (!fa->amap) {
+      RR_CUDA(cudaMemcpyAsync(h, bin, (size_t)F * NK * sizeof(C), cudaMemcpyDeviceToDevice,
+                              fa->stream));
+    } else {
+      for (int a = 0; a < fa->Fa; ++a) {
+        const size_t o = (size_t)fa->amap_h[a] * NK;
+        RR_CUDA(cudaMemcpyAsync(h + o, bin + o, NK * sizeof(C), cudaMemcpyDeviceToDevice,
+                                fa->stream));
+      }
+    }
     for (int i = 0; i + 1 < nx; ++i) {
       if ((s = gemm_step<T, true, EPI_TMP>(fa, k, kp, RT, 0, i, G + i * bb, gstride,
                                           h + (size_t)i * b * k, NK, nullptr, tb2, tstride)) !=
           RR_OK)
         return s;
       prof_count(1);
-      adj_couple_kernel<T><<<blocks, 256, 0, fa->stream>>>(view(d), i, k, tb2, tstride, h, F);
+      adj_couple_kernel<T><<<dim3((b * k + 255) / 256, active_count(fa)), 256, 0, fa->stream>>>(
+          view(d), i, k, tb2, tstride, h, fa->amap);
     }
     for (int i = nx - 1; i >= 0; --i) {
       const C* rhs = h + (size_t)i * b * k;
