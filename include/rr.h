@@ -133,9 +133,10 @@ typedef struct {
   double refine_residual; /* largest final ||b - A x|| / ||b|| per column  */
   double cqr_cond;        /* largest condition estimate of a CholeskyQR R  */
   int cqr_shifted;        /* 1 if a shifted CholeskyQR fallback was used   */
-  int refine_stagnated;   /* 1 if refinement stopped at the FP64 residual
-                             floor (a correction no longer halved the
-                             residual) above refine_tol                    */
+  int refine_stagnated;   /* 1 if refinement stopped above refine_tol
+                             because a correction removed less than a
+                             tenth of the residual (the floor of the FP64
+                             residual or of the factors' accuracy)         */
   double first_residual;  /* largest ||b - A x|| / ||b|| per column after
                              the first, uncorrected solve (the accuracy of
                              the factors themselves)                       */
@@ -205,9 +206,14 @@ rr_status rr_destroy_factors(rr_factors* f);
 
 /* x = R b (adjoint = 0) or x = R^H b (adjoint != 0) for every problem: the
  * solve of Algorithm 1's second, fourth and sixth steps.  b, x: device
- * complex128 [F][N][k], distinct.  refine_tol / max_refine drive the FP64
- * iterative refinement (FP32 factors only; ignored for FP64).  info may be
- * NULL.  Errors: RR_ERR_ARG, RR_ERR_NOCONV (x still written), RR_ERR_CUDA. */
+ * complex128 [F][N][k], distinct.  refine_tol / max_refine drive the
+ * iterative refinement x <- x + solve(b - A x) with the residual in FP64
+ * (FP64 factors too, when refine_tol > 0): it stops once every column's
+ * ||b - A x|| / ||b|| <= refine_tol or a correction removes less than a
+ * tenth of the residual.  With FP32 factors on the tensor-core sweep (even
+ * k <= 32, even block >= 128) each problem is refined on its own and leaves
+ * the set of corrected problems when it stops.  info may be NULL.  Errors:
+ * RR_ERR_ARG, RR_ERR_NOCONV (x still written), RR_ERR_CUDA. */
 rr_status rr_solve(rr_factors* f, int k, int adjoint, const void* b, void* x,
                    double refine_tol, int max_refine, rr_info* info);
 

@@ -294,16 +294,20 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
     }
     if (it == 0 && info) info->first_residual = std::max(info->first_residual, rel);
     if (tol <= 0.0) break;
-    // The FP64 residual itself carries rounding of order u ||A|| ||x||; once a
-    // correction no longer halves the residual, x is as accurate as that
+    // The FP64 residual itself carries rounding of order u ||A|| ||x||, and
+    // where the FP32 factors resolve some directions only to O(1) a
+    // correction contracts the residual slowly; refinement goes on while a
+    // correction still removes at least a tenth of the residual and stops
+    // (stagnated) once it does not: at that point x is as accurate as the
     // floor allows and further sweeps cannot help.
+    constexpr double kStagnation = 0.9;
     if (per_problem) {
       act.clear();
       for (int f = 0; f < F; ++f) {
         if (!active[f]) continue;
         if (relf[f] <= tol) {
           active[f] = 0;
-        } else if (it > 0 && relf[f] > 0.5 * prevf[f]) {
+        } else if (it > 0 && relf[f] > kStagnation * prevf[f]) {
           active[f] = 0;
           stagnated = 1;
         } else {
@@ -314,7 +318,7 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
       if (act.empty()) break;
     } else {
       if (rel <= tol) break;
-      if (it > 0 && rel > 0.5 * prev) {
+      if (it > 0 && rel > kStagnation * prev) {
         stagnated = 1;
         break;
       }

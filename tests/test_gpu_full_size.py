@@ -16,6 +16,8 @@ bench times.
   the recovery identity of Eq. 8 with identity weights) -- plus properties
   that hold at any size (orthonormal V, sorted gains, sigma_1 >=
   sigma_1^Halko), and the FP64 GPU path on one frequency (1e-6 relative).
+  Every solve of both paths ends at relative residual <= 1e-10 per column,
+  or at the FP64 residual floor where that lies above (at most 2e-10).
 * The differentiation workload at its size (256 x 128, 16 frequencies,
   k = 16, chunks of 4): the autograd gradient against central differences
   (h = 1e-6) of the objective on the first 4 of its 64 random directions.
@@ -83,7 +85,13 @@ def test_mixed_workload_at_full_size_in_the_bench_configuration(env):
     U, sig, i2 = fa.modes(V)
     torch.cuda.synchronize()
     for info in (i1, i2):
-        assert info["refine_residual"] <= 1e-10 or info["refine_stagnated"]
+        # the workload's bar is relative residual <= 1e-10 per column; where
+        # the FP64 residual's own rounding floor lies above it, refinement
+        # stops there (measured: the adjoint sketch solve at omega = 0.50
+        # ends at 1.35e-10 here and at 1.29e-10 with FP64 factors refined in
+        # FP64), so the check allows that floor and no more
+        assert info["refine_residual"] <= 2e-10, info
+        assert info["refine_residual"] <= 1e-10 or info["refine_stagnated"], info
     sig_h, sh_h = sig.cpu().numpy(), sh.cpu().numpy()
     f_hi = int(np.argmax(wl.omegas > 3.0))
     V_h = {f: V[f].cpu().numpy() for f in (0, f_hi)}
@@ -124,8 +132,10 @@ def test_mixed_workload_at_full_size_in_the_bench_configuration(env):
 
     # the FP64 GPU path on the lowest frequency
     f64 = rr.Factors(o, shifts[:1], "fp64")
-    V64, sh64, _ = f64.sketch(k, seeds[:1], phi)
-    U64, sig64, _ = f64.modes(V64)
+    V64, sh64, j1 = f64.sketch(k, seeds[:1], phi)
+    U64, sig64, j2 = f64.modes(V64)
+    for info in (j1, j2):
+        assert info["refine_residual"] <= 2e-10, info
     np.testing.assert_allclose(sig_h[0], sig64.cpu().numpy()[0], rtol=1e-6)
     np.testing.assert_allclose(sh_h[0], sh64.cpu().numpy()[0], rtol=1e-6)
     f64.close()
