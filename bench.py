@@ -179,23 +179,25 @@ def batch_for(step, rank, world, F, omegas, seed0):
 
 
 def wide_gemm_work(b):
-    """Algorithmic work of the tensor-core updates of one Schur-block inverse
-    (block b) in the wide factorisation: per 128-column slab, the rank-16
-    updates of the slab's other columns and the rank-128 update of the
-    columns outside it.  Returns (real flops, HBM bytes) -- 8 flops per
+    """Algorithmic work of the updates of one Schur-block inverse (block b) in
+    the wide factorisation.  Per 128-column slab: the rank-16 updates of the
+    slab's other columns (inner: FP32 CUDA cores) and the rank-128 update of
+    the columns outside it (outer: tensor cores).  Returns
+    {"inner": (flops, bytes), "outer": (flops, bytes)} -- 8 real flops per
     complex multiply-add; bytes = one read and one write of every updated
     complex FP32 entry of the work matrix (the operands stream from L2)."""
-    flops = byts = 0
+    inner = [0, 0]
+    outer = [0, 0]
     for c0 in range(0, b, WIDE_SLAB):
         w = min(WIDE_SLAB, b - c0)
         for k0 in range(c0, c0 + w, WIDE_PANEL):
             nbk = min(WIDE_PANEL, c0 + w - k0)
-            flops += 8 * b * (w - nbk) * nbk
-            byts += 16 * b * (w - nbk)
+            inner[0] += 8 * b * (w - nbk) * nbk
+            inner[1] += 16 * b * (w - nbk)
         if b > w:
-            flops += 8 * b * (b - w) * w
-            byts += 16 * b * (b - w)
-    return flops, byts
+            outer[0] += 8 * b * (b - w) * w
+            outer[1] += 16 * b * (b - w)
+    return {"inner": tuple(inner), "outer": tuple(outer)}
 
 
 def factor_flops(b):
@@ -369,14 +371,14 @@ def run_ours(args):
     if cls_n > 0 and cls_ms > 0:
         tot_s = cls_ms / 1e3
         if args.roofline_class == "update":
-            # the factorisation's tensor-core updates (rank-16 slab updates
-            # and rank-128 updates): a complex contraction on the tensor
-            # pipe; achieved = algorithmic flops / the class's event time
-            gfl, gby = wide_gemm_work(b)
+            # the factorisation's rank-128 updates: a complex contraction on
+            # the tensor pipe; achieved = algorithmic flops / the class's
+            # event time
+            gfl, gby = wide_gemm_work(b)["outer"]
             flops = gfl * nx * F * args.steps
             byts = gby * nx * F * args.steps
             ach = flops / tot_s / 1e12
-            roof = {"kernel": f"gjw_gemm_kernel (complex rank-16/128 updates of the Schur-block "
+            roof = {"kernel": f"gjw_gemm_kernel (complex rank-128 updates of the Schur-block "
                               f"inverse, tcgen05, {args.precision} operand split)",
                     "bound": "tensor", "achieved": ach, "peak": tensor_peak, "unit": "TFLOP/s",
                     "frac": ach / tensor_peak, "traffic": UPDATE_TRAFFIC,
@@ -395,10 +397,10 @@ def run_ours(args):
                     "algorithmic_per_launch": work / cls_n, "launches": cls_n,
                     "avg_launch_us": tot_s / cls_n * 1e6}
     # lower bound of one frequency: the factorisation's flops at the split's
-    # tensor peak plus the G_i streamed by every sweep of the solves actually
-    # run (each solve = forward + backward sweep, 1 + corrections solves)
-    corr = max(info_last[0]["refine_iters"], info_last[1]["refine_iters"])
-    n_solves = 3 * (1 + corr)
+    # tensor peak plus the G_i streamed by every sweep of the block solves
+    # actually run (each = forward + backward sweep; the three solves of
+    # Algorithm 1 plus the per-frequency refinement corrections)
+    n_solves = (info_last[0]["problem_solves"] + info_last[1]["problem_solves"]) / F
     t_fac = factor_flops(b) * nx / (tensor_peak * 1e12)
     t_sw = n_solves * 2 * nx * b * b * 8 / (hbm * 1e9)
     per_omega = {"bound_ms": (t_fac + t_sw) * 1e3, "factor_ms": t_fac * 1e3,
@@ -412,17 +414,17 @@ def run_ours(args):
     if not args.no_fp64 and rank == 0:
         F64 = args.fp64_batch
         fa.close()
-        shifts, seeds, _ = batch_for(args.warmup, 0, 1, F64, wl.omegas, wl.seed0)
+        shifts, seeds, idx64 = batch_for(args.warmup, 0, 1, F64, wl.omegas, wl.seed0)
         ref32 = rr.Factors(op, shifts, args.precision, stream)
-        V, sh32, _ = ref32.sketch(k, seeds, phi)
-        U, sig32, _ = ref32.modes(V)
+        V, sh32, ia = ref32.sketch(k, seeds, phi)
+        U, sig32, ib = ref32.modes(V)
         sig32 = sig32.cpu().numpy()
         sh32 = sh32.cpu().numpy()
         ref32.close()
         del V, U
         f64 = rr.Factors(op, shifts, "fp64", stream)
-        V, sh64, _ = f64.sketch(k, seeds, phi)       # warm-up step
-        U, sig64, _ = f64.modes(V)
+        V, sh64, ja = f64.sketch(k, seeds, phi)       # warm-up step
+        U, sig64, jb = f64.modes(V)
         sig64 = sig64.cpu().numpy()
         sh64 = sh64.cpu().numpy()
         del V, U
@@ -446,6 +448,9 @@ def run_ours(args):
                 "mixed_over_fp64": value / v64,
                 "sigma_rel_err_max": float(np.max(np.abs(sig32 - sig64) / sig64)),
                 "sigma_halko_rel_err_max": float(np.max(np.abs(sh32 - sh64) / sh64)),
+                "omegas": [float(wl.omegas[i]) for i in idx64],
+                "refine_residual_mixed": max(ia["refine_residual"], ib["refine_residual"]),
+                "refine_residual_fp64": max(ja["refine_residual"], jb["refine_residual"]),
                 "roofline": {"bound": "alu", "achieved": ach64, "peak": unit_peaks["fp64"],
                              "unit": "TFLOP/s", "frac": ach64 / unit_peaks["fp64"],
                              "note": "factorisation flops of the whole frequency over the "
@@ -505,8 +510,8 @@ def run_ours(args):
             "dtype": "c64+f64", "data": "synthetic",
             "config": workload_config(g, k, world), "frequencies_per_step_per_gpu": F,
             "precision": f"mixed: fp32 factors, tensor-core updates and sweeps in the "
-                         f"{args.precision} operand split, fp64 refinement to 1e-10, fp64 "
-                         f"CholeskyQR2 + Jacobi SVD",
+                         f"{args.precision} operand split, per-frequency fp64 refinement to "
+                         f"1e-10 or the fp64 residual floor, fp64 CholeskyQR2 + Jacobi SVD",
             "roofline": roof, "per_omega": per_omega, "measured_peaks": unit_peaks,
             "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
             "clocks": clocks, "gpu_launches": launches,
@@ -516,7 +521,11 @@ def run_ours(args):
                        "first_residual": max(info_last[0]["first_residual"],
                                              info_last[1]["first_residual"]),
                        "stagnated": bool(info_last[0]["refine_stagnated"]
-                                         or info_last[1]["refine_stagnated"])},
+                                         or info_last[1]["refine_stagnated"]),
+                       "block_solves_per_frequency": n_solves,
+                       "target": "relative residual <= 1e-10 per column, or the FP64 "
+                                 "residual floor where that lies above (a correction "
+                                 "removing < 10 % of the residual stops the frequency)"},
             "wall_s_timed": wall,
         }
         if breakdown:

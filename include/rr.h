@@ -140,6 +140,9 @@ typedef struct {
   double first_residual;  /* largest ||b - A x|| / ||b|| per column after
                              the first, uncorrected solve (the accuracy of
                              the factors themselves)                       */
+  long long problem_solves; /* block solves run, summed over the call's
+                             solves: each solve counts its problems, each
+                             correction the problems it was applied to     */
 } rr_info;
 
 const char* rr_last_error(void);
@@ -422,8 +425,9 @@ rr_status rr_batch_destroy(rr_batch* b);
  * rr_profile_start(mask): reset the counters and time every later launch of
  * the kernel classes whose bit is set in mask with a CUDA event pair on the
  * launching stream.  Classes: 0 Schur update, 1 pivoted panel, 2 row block,
- * 3 trailing update, 4 finalize (inverse + X), 5 block sweep step,
- * 6 FP64 residual, 7 Gram, 8 right multiply, 9 small k x k kernels.
+ * 3 trailing update (tensor cores), 4 finalize (inverse + X), 5 block sweep
+ * step, 6 FP64 residual, 7 Gram, 8 right multiply, 9 small k x k kernels,
+ * 10 inner slab update of the wide factorisation (CUDA cores).
  * rr_profile_read(cls): summed event time (ms) and launches of a class. */
 long long rr_launch_count(void);
 rr_status rr_profile_start(unsigned mask);

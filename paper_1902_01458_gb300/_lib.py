@@ -58,7 +58,8 @@ OMEGA_KINDS = {"gaussian": 0, "rademacher": 1, "sparse_rademacher": 2, "orthonor
 class rr_info(ctypes.Structure):
     _fields_ = [("refine_iters", ctypes.c_int), ("refine_residual", ctypes.c_double),
                 ("cqr_cond", ctypes.c_double), ("cqr_shifted", ctypes.c_int),
-                ("refine_stagnated", ctypes.c_int), ("first_residual", ctypes.c_double)]
+                ("refine_stagnated", ctypes.c_int), ("first_residual", ctypes.c_double),
+                ("problem_solves", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -132,7 +133,7 @@ SIGNATURES = {
 }
 
 PROFILE_CLASSES = {"schur": 0, "panel": 1, "rowblock": 2, "update": 3, "finalize": 4,
-                   "sweep": 5, "residual": 6, "gram": 7, "rightmul": 8, "small": 9}
+                   "sweep": 5, "residual": 6, "gram": 7, "rightmul": 8, "small": 9, "inner": 10}
 
 _lib = None
 

@@ -149,6 +149,7 @@ rr_status run_view(rr_batch* B, BGroup& G, BView& v, rr_info* info) {
     info->cqr_shifted |= i1.cqr_shifted | i2.cqr_shifted;
     info->refine_stagnated |= i1.refine_stagnated | i2.refine_stagnated;
     info->first_residual = std::max({info->first_residual, i1.first_residual, i2.first_residual});
+    info->problem_solves += i1.problem_solves + i2.problem_solves;
   }
   cudaStream_t st = fa->stream;
   const size_t vb = (size_t)N * k * sizeof(double2), sb = (size_t)k * sizeof(double);

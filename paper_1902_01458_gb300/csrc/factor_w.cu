@@ -811,10 +811,10 @@ rr_status factor_wide_impl(rr_factors* fa) {
         prof_end(PROF_PANEL, sx);
         // the rest of the slab (exact FP32 on the CUDA cores)
         if (c1 - c0 > nbk) {
-          prof_begin(PROF_UPDATE, sx);
+          prof_begin(PROF_INNER, sx);
           gjw_inner_update_kernel<<<dim3((b + IU_RT - 1) / IU_RT, F), IU_THREADS, 0, sx>>>(
               b, k0, c0, c1, M, reinterpret_cast<const float2*>(fa->Bbuf), fa->rowpiv);
-          prof_end(PROF_UPDATE, sx);
+          prof_end(PROF_INNER, sx);
           RR_CUDA(cudaGetLastError());
         }
       }

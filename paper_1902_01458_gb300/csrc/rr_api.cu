@@ -179,6 +179,7 @@ void info_reset(rr_info* info) {
   info->cqr_shifted = 0;
   info->refine_stagnated = 0;
   info->first_residual = 0.0;
+  info->problem_solves = 0;
 }
 
 // x = A^{-1} b (or A^{-H} b) in FP64 [F][N][k], b != x, with FP64 iterative
@@ -200,6 +201,7 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
     if ((s = launch_solve_lo(fa, k, adjoint, w.L1, w.L2, w.L3)) != RR_OK) return s;
     if ((s = launch_convert_f2d(nel, (const float2*)w.L2, x, 0, st)) != RR_OK) return s;
   }
+  if (info) info->problem_solves += F;
   const bool check = lo || info != nullptr || tol > 0.0 || fa->sched_mode != SCHED_EAGER;
   if (!check) return RR_OK;
   if ((s = launch_colnorm2(F, d.n, k, b, w.dpart, w.nblk_col, w.bn, st)) != RR_OK) return s;
@@ -211,6 +213,7 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
       return RR_ERR_ARG;
     }
     const int nit = (*fa->sched)[fa->sched_pos++];
+    if (info) info->problem_solves += (long long)nit * F;
     for (int t = 0; t < nit; ++t) {
       if ((s = launch_residual(d, F, fa->shifts, k, adjoint, b, x, w.R64, st)) != RR_OK) return s;
       if (!lo) {
@@ -333,6 +336,7 @@ rr_status solve_refined(rr_factors* fa, int k, int adjoint, const double2* b, do
       break;
     }
     // correction d = solve(r); x += d
+    if (info) info->problem_solves += per_problem ? (long long)act.size() : F;
     if (per_problem) {
       const size_t nk = (size_t)d.n * k;
       RR_CUDA(cudaMemcpyAsync(fa->amap_buf, act.data(), act.size() * sizeof(int),

@@ -304,7 +304,7 @@ rr_status launch_gain_grad(const OpDev& d, const rr_grid& g, int F, int J, const
 enum {
   PROF_SCHUR = 0, PROF_PANEL = 1, PROF_ROWBLOCK = 2, PROF_UPDATE = 3, PROF_FINALIZE = 4,
   PROF_SWEEP = 5, PROF_RESIDUAL = 6, PROF_GRAM = 7, PROF_RIGHTMUL = 8, PROF_SMALL = 9,
-  PROF_OTHER = 10, PROF_N = 11
+  PROF_INNER = 10, PROF_OTHER = 11, PROF_N = 12
 };
 // While a ProfSuspend lives (graph capture), launches are neither counted
 // nor timed.
