@@ -62,13 +62,18 @@ def parse():
     p.add_argument("--nx", type=int, default=512)
     p.add_argument("--ny", type=int, default=256)
     p.add_argument("--k", type=int, default=32)
-    p.add_argument("--roofline-class", default="update")
+    p.add_argument("--roofline-class", default="sweep", choices=["sweep", "update"],
+                   help="kernel class of the reported roofline (the other goes to "
+                        "roofline_other)")
     p.add_argument("--precision", default="fp32", choices=list(PRECISIONS),
                    help="operand split of the FP32 factors' tensor-core products")
     p.add_argument("--fp64-steps", type=int, default=2)
-    p.add_argument("--workload", default="mixed", choices=["mixed", "batched"],
+    p.add_argument("--workload", default="mixed", choices=["mixed", "batched", "gradient"],
                    help="mixed: 512x256, k=32, 64 frequencies (default); "
-                        "batched: the 128-problem uneven batch as one graph")
+                        "batched: the 128-problem uneven batch as one graph; "
+                        "gradient: d(sum of leading gains)/d(base flow) at 256x128")
+    p.add_argument("--fd-directions", type=int, default=64,
+                   help="gradient: random directions checked by central differences")
     p.add_argument("--tune", type=int, default=1, help="batched: autotune the plan")
     p.add_argument("--breakdown", action="store_true",
                    help="one extra profiled step with every kernel class timed")
@@ -331,20 +336,23 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     barrier(pg, local)
     torch.cuda.synchronize(dev)
-    _lib.rr_profile_start([args.roofline_class])
+    roof_classes = ["sweep", "update"]
+    _lib.rr_profile_start(roof_classes)
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
+    solves_timed = 0   # block solves of one problem (Algorithm 1's three + corrections)
     with Clocks(local) as clk:
         start.record(stream)
         t0 = time.perf_counter()
         for s in range(args.steps):
             sig, sh, i1, i2 = step(fa, args.warmup + s)
             info_last = (i1, i2)
+            solves_timed += i1["problem_solves"] + i2["problem_solves"]
         end.record(stream)
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
     launches = _lib.rr_launch_count()
-    cls_ms, cls_n = _lib.rr_profile_read(args.roofline_class)
+    cls_read = {c: _lib.rr_profile_read(c) for c in roof_classes}
     _lib.rr_profile_start([])
     elapsed_ms = start.elapsed_time(end)
     barrier(pg, local)
@@ -362,40 +370,50 @@ def run_ours(args):
         breakdown = {c: dict(zip(("ms", "launches"), _lib.rr_profile_read(c))) for c in allc}
         _lib.rr_profile_start([])
 
-    # roofline of the timed kernel class
+    # rooflines of the two largest kernel classes, timed in the timed region
     b, nx = g.b, g.nx
     hbm, bf16, src = peaks()
     unit, nmma = SPLIT_MMAS[args.precision]
     tensor_peak = unit_peaks[unit] / nmma   # FP32-level flops of the split
-    roof = None
-    if cls_n > 0 and cls_ms > 0:
-        tot_s = cls_ms / 1e3
-        if args.roofline_class == "update":
-            # the factorisation's rank-128 updates: a complex contraction on
-            # the tensor pipe; achieved = algorithmic flops / the class's
-            # event time
-            gfl, gby = wide_gemm_work(b)["outer"]
-            flops = gfl * nx * F * args.steps
-            byts = gby * nx * F * args.steps
-            ach = flops / tot_s / 1e12
-            roof = {"kernel": f"gjw_gemm_kernel (complex rank-128 updates of the Schur-block "
-                              f"inverse, tcgen05, {args.precision} operand split)",
-                    "bound": "tensor", "achieved": ach, "peak": tensor_peak, "unit": "TFLOP/s",
-                    "frac": ach / tensor_peak, "traffic": UPDATE_TRAFFIC,
-                    "peak_source": f"measured {unit} MMA peak {unit_peaks[unit]:.0f} TFLOP/s "
-                                   f"(rr_measure_peak) / {nmma} MMAs per FP32-level product",
-                    "algorithmic_per_launch": flops / cls_n, "launches": cls_n,
-                    "avg_launch_us": tot_s / cls_n * 1e6,
-                    "hbm_achieved_gbs": byts / tot_s / 1e9, "hbm_frac": byts / tot_s / 1e9 / hbm,
-                    "hbm_peak_source": src}
-        elif args.roofline_class == "sweep":
-            work = F * (b * b * 8 + 3 * b * k * 8) * cls_n
-            ach = work / tot_s / 1e9
-            roof = {"kernel": "sweep_tc2_kernel + combine (one streamwise column, tcgen05)",
-                    "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": SWEEP_TRAFFIC, "peak_source": src,
-                    "algorithmic_per_launch": work / cls_n, "launches": cls_n,
-                    "avg_launch_us": tot_s / cls_n * 1e6}
+    rooflines = {}
+    ms_sw, n_sw = cls_read["sweep"]
+    if n_sw > 0 and ms_sw > 0:
+        # every block solve of one problem streams G_i of each streamwise
+        # column once forward and once backward (2 nx - 1 column steps) plus
+        # its right-hand side, result and the K-split partial blocks
+        tot_s = ms_sw / 1e3
+        work = solves_timed * (2 * nx - 1) * (b * b * 8 + 3 * b * k * 8)
+        ach = work / tot_s / 1e9
+        rooflines["sweep"] = {
+            "kernel": "sweep_tc2_kernel + sweep_combine_kernel (one streamwise column step "
+                      "of the active frequencies, tcgen05)",
+            "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": SWEEP_TRAFFIC, "peak_source": src,
+            "algorithmic_per_launch": work / n_sw, "launches": n_sw,
+            "avg_launch_us": tot_s / n_sw * 1e6,
+            "algorithmic_note": "per block solve of one problem: (2 nx - 1) x (b^2 x 8 B of "
+                                "G_i + 3 b k x 8 B of vectors)"}
+    ms_up, n_up = cls_read["update"]
+    if n_up > 0 and ms_up > 0:
+        # the factorisation's rank-128 updates: a complex contraction on the
+        # tensor pipe; achieved = algorithmic flops / the class's event time
+        tot_s = ms_up / 1e3
+        gfl, gby = wide_gemm_work(b)["outer"]
+        flops = gfl * nx * F * args.steps
+        byts = gby * nx * F * args.steps
+        ach = flops / tot_s / 1e12
+        rooflines["update"] = {
+            "kernel": f"gjw_gemm_kernel (complex rank-128 updates of the Schur-block "
+                      f"inverse, tcgen05, {args.precision} operand split)",
+            "bound": "tensor", "achieved": ach, "peak": tensor_peak, "unit": "TFLOP/s",
+            "frac": ach / tensor_peak, "traffic": UPDATE_TRAFFIC,
+            "peak_source": f"measured {unit} MMA peak {unit_peaks[unit]:.0f} TFLOP/s "
+                           f"(rr_measure_peak) / {nmma} MMAs per FP32-level product",
+            "algorithmic_per_launch": flops / n_up, "launches": n_up,
+            "avg_launch_us": tot_s / n_up * 1e6,
+            "hbm_achieved_gbs": byts / tot_s / 1e9, "hbm_frac": byts / tot_s / 1e9 / hbm,
+            "hbm_peak_source": src}
+    roof = rooflines.get(args.roofline_class)
     # lower bound of one frequency: the factorisation's flops at the split's
     # tensor peak plus the G_i streamed by every sweep of the block solves
     # actually run (each = forward + backward sweep; the three solves of
@@ -512,7 +530,9 @@ def run_ours(args):
             "precision": f"mixed: fp32 factors, tensor-core updates and sweeps in the "
                          f"{args.precision} operand split, per-frequency fp64 refinement to "
                          f"1e-10 or the fp64 residual floor, fp64 CholeskyQR2 + Jacobi SVD",
-            "roofline": roof, "per_omega": per_omega, "measured_peaks": unit_peaks,
+            "roofline": roof,
+            "roofline_other": {c: r for c, r in rooflines.items() if c != args.roofline_class},
+            "per_omega": per_omega, "measured_peaks": unit_peaks,
             "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
             "clocks": clocks, "gpu_launches": launches,
             "refine": {"iters": max(info_last[0]["refine_iters"], info_last[1]["refine_iters"]),
@@ -606,12 +626,101 @@ def run_batched(args):
         pg.destroy_process_group()
 
 
+def run_gradient(args):
+    """The differentiation workload: J = sum over 16 frequencies of the 3
+    leading gains at 256 x 128 (k = 16, two subspace iterations, FP64
+    factors recomputed per 4-frequency chunk) and its gradient with respect to
+    the nodal base flow (rho, U, V) through the autograd function.  One step
+    = forward + backward.  After the timed steps the gradient is checked
+    against central differences (h = 1e-6) of the same objective on the
+    workload's random directions (error relative to the rms directional
+    derivative).  Rank 0 only (a single-GPU workload)."""
+    import torch
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_1902_01458_gb300 import build as rrbuild
+    if rank == 0:
+        rrbuild.build()
+    barrier(pg, local)
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    import paper_1902_01458_gb300 as rr
+    from paper_1902_01458_gb300 import _lib
+    from paper_1902_01458_gb300.autograd import gain_objective
+    rr.load()
+    wl = W.config_gradient()
+    g, base = wl.grid, wl.flow
+    seeds = [wl.seed0 + i for i in range(len(wl.omegas))]
+    kw = dict(grid=g, omegas=wl.omegas, k=wl.k, J=wl.J, seeds=seeds, chunk=wl.chunk,
+              precision="fp64", power_iters=2)
+
+    def grad_step():
+        fields = [torch.tensor(a, dtype=torch.float64, requires_grad=True)
+                  for a in (base.rho, base.u, base.v)]
+        val = gain_objective(*fields, **kw)
+        val.backward()
+        return float(val), np.stack([f.grad.numpy() for f in fields])
+
+    for _ in range(args.warmup):
+        grad_step()
+    torch.cuda.synchronize(dev)
+    _lib.rr_profile_start([])
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            val, grad = grad_step()
+        torch.cuda.synchronize(dev)
+        t_step = (time.perf_counter() - t0) / args.steps
+    launches = _lib.rr_launch_count()
+    # central differences on the workload's directions
+    an, fd = [], []
+    t1 = time.perf_counter()
+    for d in W.gradient_directions(wl, args.fd_directions):
+        def at(t):
+            with torch.no_grad():
+                f = [torch.tensor(a + t * dd) for a, dd in zip((base.rho, base.u, base.v), d)]
+                return float(gain_objective(*f, **dict(kw, chunk=len(wl.omegas))))
+        fd.append((at(wl.h) - at(-wl.h)) / (2 * wl.h))
+        an.append(float(np.sum(grad * d)))
+    t_fd = time.perf_counter() - t1
+    an, fd = np.array(an), np.array(fd)
+    scale = float(np.sqrt(np.mean(fd ** 2)))
+    err = np.abs(an - fd) / scale
+    rel = np.abs(an - fd) / np.maximum(np.abs(fd), 1e-300)
+    line = {
+        "metric": "gain-gradient evaluations/sec (16 frequencies, 256x128, k=16, J=3)",
+        "value": 1.0 / t_step, "unit": "gradients/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "ns2d-256x128-k16-grad", "N": g.n, "frequencies":
+                   len(wl.omegas), "k": wl.k, "J": wl.J, "chunk": wl.chunk,
+                   "power_iters": 2, "parallelism": "single GPU"},
+        "timing": "host wall clock around forward + backward (autograd, includes the "
+                  "host-side chunk loop), CUDA synchronised",
+        "objective": val, "clocks": clk.summary(), "gpu_launches": launches,
+        "fd_check": {"directions": int(len(fd)), "h": wl.h,
+                     "max_err_over_rms": float(err.max()),
+                     "median_rel_err": float(np.median(rel)),
+                     "bar": "max |grad.d - FD(d)| <= 1e-5 x rms FD, median rel <= 1e-6",
+                     "passed": bool(err.max() <= 1e-5 and np.median(rel) <= 1e-6),
+                     "seconds": t_fd},
+    }
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "gradient":
+        run_gradient(args)
     else:
         run_ours(args)
 

@@ -54,10 +54,12 @@ typedef enum {
 
 /* Arithmetic of the block factorisation and the block sweeps.  FP64 runs
  * everything in complex double.  FP32 stores the factors in complex float,
- * runs the factorisation's updates and the sweep products on the tensor
- * cores (tcgen05 kind::tf32 with each operand split into a TF32 part and its
- * remainder, hi.hi + hi.lo + lo.hi: FP32-level products, FP32 accumulation)
- * and wins accuracy back by iterative refinement against an FP64 residual.
+ * runs the factorisation's rank-128 updates and the sweep products on the
+ * tensor cores (tcgen05 kind::tf32 with each operand split into a TF32 part
+ * and its remainder, hi.hi + hi.lo + lo.hi: FP32-level products, FP32
+ * accumulation; the pivoted panels and the rank-16 updates inside a
+ * 128-column slab run in FP32 on the CUDA cores) and wins accuracy back by
+ * iterative refinement against an FP64 residual.
  * FP32_BF16X3 and FP32_BF16X6 are the same with the operands split into
  * BF16 pieces on tcgen05 kind::f16: two pieces and three products (about 16
  * bits of each product) or three pieces and six products (hi.hi, hi.mid,
