@@ -44,20 +44,22 @@ namespace {
 constexpr int GW_W = 128;   // slab width (rank of the outer update)
 constexpr int GW_NB = 16;   // panel width (rank of the inner update)
 constexpr int GW_PANEL_MAX = 768;  // rows a panel CTA holds (two per thread)
-constexpr int GW_BIN_ROWS = 32;    // row pitch per problem of the inner update's B buffer
 
 // ------------------------------------------------------------------- panel
-// Eliminates columns [k0, k0 + nbk) of every row of M (problem = blockIdx.x).
-// Thread t holds the nbk entries of row t (RPT = 1; RPT = 2 would hold rows
-// t and t + blockDim.x) in registers.  Per column j: each warp finds its best
-// eligible row (largest |.|^2, lowest row on ties) and the winning lane
-// publishes that whole row in shared memory; after one block barrier every
-// warp reduces the per-warp candidates itself, reads the pivot row from
-// shared memory and eliminates (candidates double-buffered by step parity).
-// Outputs: the panel columns of M, rowpiv[r] = pivot column of the rows
-// pivoted here, pivslot[k0 + j] = pivot row of column k0 + j, and Bin =
-// M_old[P, slab] with the panel's own columns (and columns outside the slab)
-// zero: the right operand of the inner update.
+// Eliminates columns K = [k0, k0 + nbk) of every row of M (problem =
+// blockIdx.x), one row per thread, the row's 16 entries of K held in
+// registers.  When kp0 >= 0 the previous panel [kp0, kp0 + 16) of the same
+// slab was factored last and its transformation has reached every slab
+// column except its own and K (gjw_slab_update_kernel); the kernel applies
+// it to K first:
+//   x += M[r, Kp] B   (rows not pivoted in Kp),   x = M[r, Kp] B   (its pivot rows),
+// B = the rows of Kp's pivots at K before this step.  Then per column j:
+// each warp finds its best eligible row (largest |.|^2, lowest row on ties)
+// and the winning lane publishes that whole row in shared memory; after one
+// block barrier every warp reduces the per-warp candidates itself, reads the
+// pivot row from shared memory and eliminates (candidates double-buffered
+// by step parity).  Outputs: the columns K of M, rowpiv[r] = pivot column of
+// the rows pivoted here, pivslot[k0 + j] = pivot row of column k0 + j.
 constexpr int GW_PANEL_THREADS = GW_PANEL_MAX;  // one row per thread up to 768 rows
 
 // rotate a held row left by one place (column c + 1 moves to register c)
@@ -72,55 +74,71 @@ __device__ __forceinline__ void gjw_rotate(float2 (&x)[GW_NB]) {
 // threads of a warp, one row each, spread over the banks)
 constexpr int GW_STAGE_LD = GW_NB + 2;
 
-__device__ __forceinline__ void gjw_take_row(const float2* stage, int row, bool ok,
-                                             float2 (&x)[GW_NB]) {
-#pragma unroll
-  for (int c = 0; c < GW_NB; ++c)
-    x[c] = ok ? stage[row * GW_STAGE_LD + c] : make_float2(0.f, 0.f);
+// the 16 columns [c, c + ncol) of every row of M into the stage (zero
+// beyond ncol), each warp reading whole 128-byte row segments
+__device__ __forceinline__ void gjw_stage_cols(float2* stage, const float2* M, int b, int c,
+                                               int ncol) {
+  for (int e = threadIdx.x; e < b * (GW_NB / 2); e += blockDim.x) {
+    const int row = e / (GW_NB / 2), u = e - row * (GW_NB / 2);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (2 * u < ncol) v = reinterpret_cast<const float4*>(M + (size_t)row * b + c)[u];
+    *reinterpret_cast<float4*>(&stage[row * GW_STAGE_LD + 2 * u]) = v;
+  }
 }
 
-__device__ __forceinline__ void gjw_put_row(float2* stage, int row, bool ok,
-                                            const float2 (&x)[GW_NB]) {
-  if (!ok) return;
-#pragma unroll
-  for (int c = 0; c < GW_NB; ++c) stage[row * GW_STAGE_LD + c] = x[c];
-}
-
-template <int RPT>
 __global__ void __launch_bounds__(GW_PANEL_THREADS, 1)
-gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Mall,
+gjw_panel_kernel(int b, int k0, int nbk, int kp0, float2* __restrict__ Mall,
                  int* __restrict__ rowpiv_all, int* __restrict__ pivslot_all,
-                 float2* __restrict__ Bin_all, int* __restrict__ flag) {
+                 int* __restrict__ flag) {
   constexpr int NB = GW_NB;
   constexpr int MAXW = GW_PANEL_THREADS / 32;
   __shared__ __align__(16) float2 cand[2][MAXW][NB];
   __shared__ float candv[2][MAXW];
   __shared__ int candi[2][MAXW];
   __shared__ int piv_sm[NB];
+  __shared__ __align__(16) float2 Bp[NB][NB];   // Kp's pivot rows at K
   extern __shared__ __align__(16) float2 stage[];  // [b][GW_STAGE_LD]
   const int f = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int nt = blockDim.x, nw = nt >> 5;
-  const int r0 = t, r1 = t + nt;  // rows held (r1 only when RPT == 2)
-  const bool a0 = r0 < b, a1 = RPT == 2 && r1 < b;
+  const int nw = blockDim.x >> 5;
+  const bool a0 = t < b;
   float2* M = Mall + (size_t)f * b * b;
   int* rowpiv = rowpiv_all + (size_t)f * b;
 
-  float2 x0[NB], x1[NB];
-  // the panel M[:, K] through shared memory: each warp reads whole 128-byte
-  // row segments (8 lanes per row), then every thread takes its row
-  for (int e = t; e < b * (NB / 2); e += nt) {
-    const int row = e / (NB / 2), u = e - row * (NB / 2);
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (2 * u < nbk) v = reinterpret_cast<const float4*>(M + (size_t)row * b + k0)[u];
-    *reinterpret_cast<float4*>(&stage[row * GW_STAGE_LD + 2 * u]) = v;
-  }
+  float2 x0[NB];
+  gjw_stage_cols(stage, M, b, k0, nbk);
   __syncthreads();
-  gjw_take_row(stage, r0, a0, x0);
-  if (RPT == 2) gjw_take_row(stage, r1, a1, x1);
-  bool e0 = a0 && rowpiv[r0] < 0;
-  bool e1 = a1 && rowpiv[r1] < 0;
-  int col0 = -1, col1 = -1;
+#pragma unroll
+  for (int c = 0; c < NB; ++c)
+    x0[c] = a0 ? stage[t * GW_STAGE_LD + c] : make_float2(0.f, 0.f);
+  const int rp = a0 ? rowpiv[t] : -1;
+  if (kp0 >= 0) {
+    const bool prevpiv = rp >= kp0 && rp < kp0 + NB;
+    if (prevpiv) {
+#pragma unroll
+      for (int c = 0; c < NB; ++c) Bp[rp - kp0][c] = x0[c];
+    }
+    __syncthreads();  // B published; every row taken from the stage
+    gjw_stage_cols(stage, M, b, kp0, NB);
+    __syncthreads();
+    if (a0) {
+      if (prevpiv) {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) x0[c] = make_float2(0.f, 0.f);
+      }
+#pragma unroll 1
+      for (int j = 0; j < NB; ++j) {
+        const float2 a = stage[t * GW_STAGE_LD + j];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) x0[c] = cfma(a, Bp[j][c], x0[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c >= nbk) x0[c] = make_float2(0.f, 0.f);
+    }
+  }
+  bool e0 = a0 && rp < 0;
+  int col0 = -1;
 
   // The step loop stays rolled (an unrolled one overflows the instruction
   // cache: every warp would run the whole straight-line program once).  The
@@ -131,31 +149,20 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
 #pragma unroll 1
   for (int j = 0; j < nbk; ++j) {
     const int buf = j & 1;
-    // this thread's best eligible row, then the warp's
-    float bv = e0 ? x0[0].x * x0[0].x + x0[0].y * x0[0].y : -1.f;
-    int bi = a0 ? r0 : 0x7fffffff;
-    if (RPT == 2) {
-      const float v1 = e1 ? x1[0].x * x1[0].x + x1[0].y * x1[0].y : -1.f;
-      if (a1 && v1 > bv) { bv = v1; bi = r1; }
-    }
-    const int mine = bi;
-    // warp argmax in two warp reductions: the largest key (the bits of a
-    // non-negative float order like the float; ineligible rows key 0), then
-    // the lowest row holding it
-    const unsigned key = bv >= 0.f ? __float_as_uint(bv) + 1u : 0u;
+    // this thread's best eligible row, then the warp's, in two warp
+    // reductions: the largest key (the bits of a non-negative float order
+    // like the float; ineligible rows key 0), then the lowest row holding it
+    const float bv0 = e0 ? x0[0].x * x0[0].x + x0[0].y * x0[0].y : -1.f;
+    const int mine = a0 ? t : 0x7fffffff;
+    const unsigned key = bv0 >= 0.f ? __float_as_uint(bv0) + 1u : 0u;
     const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
-    bi = (int)__reduce_min_sync(0xffffffffu, key == kmax ? (unsigned)bi : 0x7fffffffu);
-    bv = kmax == 0u ? -1.f : __uint_as_float(kmax - 1u);
+    const int bi = (int)__reduce_min_sync(0xffffffffu, key == kmax ? (unsigned)mine : 0x7fffffffu);
+    const float bv = kmax == 0u ? -1.f : __uint_as_float(kmax - 1u);
     if (bi == mine && bi != 0x7fffffff) {
       // 16-byte stores: the shared-memory pipe is the step's bottleneck
       float4* dst = reinterpret_cast<float4*>(cand[buf][warp]);
-      if (RPT == 2 && bi == r1) {
 #pragma unroll
-        for (int c = 0; c < NB; c += 2) dst[c / 2] = make_float4(x1[c].x, x1[c].y, x1[c + 1].x, x1[c + 1].y);
-      } else {
-#pragma unroll
-        for (int c = 0; c < NB; c += 2) dst[c / 2] = make_float4(x0[c].x, x0[c].y, x0[c + 1].x, x0[c + 1].y);
-      }
+      for (int c = 0; c < NB; c += 2) dst[c / 2] = make_float4(x0[c].x, x0[c].y, x0[c + 1].x, x0[c + 1].y);
       candv[buf][warp] = bv;
       candi[buf][warp] = bi;
     }
@@ -191,8 +198,7 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
     const float2 pinv = make_float2(piv.x * ipd, -piv.y * ipd);
     // every held row: x -= (x_0 / pivot) * pivot row, x_0 <- -x_0 / pivot;
     // the pivot row itself is scaled by 1/pivot, its x_0 <- 1/pivot
-    const bool p0 = r0 == pi, p1 = RPT == 2 && r1 == pi;
-    if (!p0) {
+    if (t != pi) {
       const float2 m0 = cmul(x0[0], pinv);
 #pragma unroll
       for (int c = 1; c < NB; ++c) {
@@ -208,131 +214,112 @@ gjw_panel_kernel(int b, int k0, int nbk, int c0, int c1, float2* __restrict__ Ma
       e0 = false;
       col0 = j;
     }
-    if (RPT == 2) {
-      if (!p1) {
-        const float2 m1 = cmul(x1[0], pinv);
-#pragma unroll
-        for (int c = 1; c < NB; ++c) {
-          const float2 p = prow[c];
-          x1[c].x = fmaf(-m1.x, p.x, fmaf(m1.y, p.y, x1[c].x));
-          x1[c].y = fmaf(-m1.x, p.y, fmaf(-m1.y, p.x, x1[c].y));
-        }
-        x1[0] = make_float2(-m1.x, -m1.y);
-      } else {
-#pragma unroll
-        for (int c = 1; c < NB; ++c) x1[c] = cmul(prow[c], pinv);
-        x1[0] = pinv;
-        e1 = false;
-        col1 = j;
-      }
-    }
     gjw_rotate(x0);
-    if (RPT == 2) gjw_rotate(x1);
   }
   // a ragged panel (nbk < NB steps) rotates the remaining NB - nbk places
 #pragma unroll 1
-  for (int j = nbk; j < NB; ++j) {
-    gjw_rotate(x0);
-    if (RPT == 2) gjw_rotate(x1);
-  }
+  for (int j = nbk; j < NB; ++j) gjw_rotate(x0);
   // panel columns back in place (through shared memory, coalesced); pivot
   // bookkeeping
-  gjw_put_row(stage, r0, a0, x0);
-  if (RPT == 2) gjw_put_row(stage, r1, a1, x1);
-  if (a0 && col0 >= 0) rowpiv[r0] = k0 + col0;
-  if (a1 && col1 >= 0) rowpiv[r1] = k0 + col1;
+  __syncthreads();  // the stage is free (the pre-step's reads are done)
+  if (a0) {
+#pragma unroll
+    for (int c = 0; c < NB; ++c) stage[t * GW_STAGE_LD + c] = x0[c];
+  }
+  if (a0 && col0 >= 0) rowpiv[t] = k0 + col0;
   __syncthreads();
-  for (int e = t; e < b * (NB / 2); e += nt) {
+  for (int e = t; e < b * (NB / 2); e += blockDim.x) {
     const int row = e / (NB / 2), u = e - row * (NB / 2);
     if (2 * u < nbk)
       reinterpret_cast<float4*>(M + (size_t)row * b + k0)[u] =
           *reinterpret_cast<const float4*>(&stage[row * GW_STAGE_LD + 2 * u]);
   }
   if (t < nbk) pivslot_all[(size_t)f * b + k0 + t] = piv_sm[t];
-  // Bin[f][c][m] = M_old[P_c][m] for m in the slab outside the panel, else 0
-  // (columns outside the slab are never read by the inner update)
-  float2* Bin = Bin_all + (size_t)f * GW_BIN_ROWS * b;
-  const int wslab = c1 - c0;
-  for (int e = t; e < NB * wslab; e += nt) {
-    const int c = e / wslab, m = c0 + (e - c * wslab);
-    float2 v = make_float2(0.f, 0.f);
-    if (c < nbk && !(m >= k0 && m < k0 + nbk)) v = M[(size_t)piv_sm[c] * b + m];
-    Bin[(size_t)c * b + m] = v;
-  }
 }
 
-// ------------------------------------------------------------ inner update
-// The transformations of panel K = [k0, k0 + 16) applied to the rest of its
-// slab, on the FP32 CUDA cores (a rank-16 contraction is bound by moving the
-// slab, not by its flops):
-//   M[r, m] += M[r, K] Bin[:, m]      rows r not pivoted in K,
-//   M[r, m]  = M[r, K] Bin[:, m]      the pivot rows of K (T^{-1} B itself),
-// for the slab columns m outside K.  CTA = (64-row tile, problem); the tile's
-// multipliers M[rows, K] and all of Bin's slab columns sit in shared memory;
-// thread (ty, tx) accumulates rows ty + 16 i (i < 4) x slab columns tx + 16 j
-// (j < 8) in registers, so each shared-memory load feeds 4 or 8 complex FMAs.
-constexpr int IU_RT = 64, IU_THREADS = 256;
+// ------------------------------------------------------------- slab update
+// The transformation of panel K = [k0, k0 + nbk) applied to the slab's other
+// columns, except the next panel's [kn0, kn0 + 16) (kn0 < 0: none), which
+// that panel's kernel updates itself:
+//   M[r, m] += M[r, K] B[:, m]      rows r not pivoted in K,
+//   M[r, m]  = M[r, K] B[:, m]      the pivot rows of K (T^{-1} B itself),
+// B[j][m] = M[pivslot[k0 + j], m] before this step.  CTA = (one 16-column
+// group of the slab, problem): it owns those columns of every row, so it
+// reads B for its columns before it writes any row (no other CTA writes
+// them).  Exact FP32 on the CUDA cores: a rank-16 contraction is bound by
+// moving the columns, not by its flops.
+constexpr int SU_THREADS = 512, SU_RT = 64;
 
-__global__ void __launch_bounds__(IU_THREADS)
-gjw_inner_update_kernel(int b, int k0, int c0, int c1, float2* __restrict__ Mall,
-                        const float2* __restrict__ Bin_all, const int* __restrict__ rowpiv_all) {
-  constexpr int NB = GW_NB, RI = IU_RT / 16, CJ = GW_W / 16;
-  __shared__ __align__(16) float2 As[IU_RT][NB + 1];
-  __shared__ __align__(16) float2 Bs[NB][GW_W];
-  const int f = blockIdx.y, r0 = blockIdx.x * IU_RT;
-  const int w = c1 - c0;
-  float2* M = Mall + (size_t)f * b * b;
-  const float2* Bin = Bin_all + (size_t)f * GW_BIN_ROWS * b;
-  // the accumulators start from the old values (zero on pivot rows), loaded
-  // first so that their latency overlaps the staging and the contraction
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int* rowpiv = rowpiv_all + (size_t)f * b;
-  float2 acc[RI][CJ];
-  unsigned upd[RI];
-#pragma unroll
-  for (int i = 0; i < RI; ++i) {
-    const int r = r0 + ty + 16 * i;
-    const int rp = r < b ? rowpiv[r] : -1;
-    const bool pivot = rp >= k0 && rp < k0 + NB;
-    const float2* Mr = M + (size_t)(r < b ? r : 0) * b + c0;
-    upd[i] = 0u;
-#pragma unroll
-    for (int j = 0; j < CJ; ++j) {
-      const int m = tx + 16 * j;
-      const bool u = r < b && m < w && !(c0 + m >= k0 && c0 + m < k0 + NB);
-      upd[i] |= u ? (1u << j) : 0u;
-      acc[i][j] = (u && !pivot) ? Mr[m] : make_float2(0.f, 0.f);
+__global__ void __launch_bounds__(SU_THREADS)
+gjw_slab_update_kernel(int b, int k0, int nbk, int kn0, int c0, int c1, float2* __restrict__ Mall,
+                       const int* __restrict__ rowpiv_all, const int* __restrict__ pivslot_all) {
+  constexpr int NB = GW_NB;
+  __shared__ float2 Bs[NB][NB + 1];
+  __shared__ float2 As[SU_RT][NB + 1];
+  const int f = blockIdx.y;
+  // blockIdx.x-th 16-column group of [c0, c1) that is neither K nor the
+  // next panel
+  int cs = -1;
+  for (int g = 0, cnt = 0; c0 + NB * g < c1; ++g) {
+    const int c = c0 + NB * g;
+    if (c == k0 || c == kn0) continue;
+    if (cnt++ == (int)blockIdx.x) {
+      cs = c;
+      break;
     }
   }
-  for (int e = threadIdx.x; e < IU_RT * NB; e += IU_THREADS) {
-    const int rr = e / NB, k = e - rr * NB, r = r0 + rr;
-    As[rr][k] = (r < b && k0 + k < b) ? M[(size_t)r * b + k0 + k] : make_float2(0.f, 0.f);
+  if (cs < 0) return;
+  const int nc = min(NB, c1 - cs);
+  float2* M = Mall + (size_t)f * b * b;
+  const int* rowpiv = rowpiv_all + (size_t)f * b;
+  const int* piv = pivslot_all + (size_t)f * b + k0;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // ty: 0 .. 31
+  for (int e = tid; e < NB * NB; e += SU_THREADS) {
+    const int j = e / NB, c = e - j * NB;
+    Bs[j][c] = (j < nbk && c < nc) ? M[(size_t)piv[j] * b + cs + c] : make_float2(0.f, 0.f);
   }
-  for (int e = threadIdx.x; e < NB * GW_W; e += IU_THREADS) {
-    const int k = e / GW_W, m = e - k * GW_W;
-    Bs[k][m] = m < w ? Bin[(size_t)k * b + c0 + m] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-#pragma unroll 4
-  for (int k = 0; k < NB; ++k) {
-    float2 a[RI], bk[CJ];
+  __syncthreads();  // every B entry read before any row (pivot rows included) is written
+  // Row tiles of SU_RT rows, software-pipelined: the old values and K's
+  // entries of tile t + 1 are loaded into registers while tile t is computed.
+  constexpr int RI = SU_RT / 32, AI = SU_RT * NB / SU_THREADS;
+  float2 old[RI], anext[AI];
+  bool pivn[RI];
+  auto load = [&](int r0) {
 #pragma unroll
-    for (int i = 0; i < RI; ++i) a[i] = As[ty + 16 * i][k];
+    for (int i = 0; i < RI; ++i) {
+      const int r = r0 + ty + 32 * i;
+      const bool live = r < b && tx < nc;
+      const int rp = live ? rowpiv[r] : -1;
+      pivn[i] = rp >= k0 && rp < k0 + NB;
+      old[i] = (live && !pivn[i]) ? M[(size_t)r * b + cs + tx] : make_float2(0.f, 0.f);
+    }
 #pragma unroll
-    for (int j = 0; j < CJ; ++j) bk[j] = Bs[k][tx + 16 * j];
+    for (int u = 0; u < AI; ++u) {
+      const int e = tid + u * SU_THREADS, rr = e / NB, k = e - rr * NB, r = r0 + rr;
+      anext[u] = (r < b && k < nbk) ? M[(size_t)r * b + k0 + k] : make_float2(0.f, 0.f);
+    }
+  };
+  load(0);
+#pragma unroll 1
+  for (int r0 = 0; r0 < b; r0 += SU_RT) {
 #pragma unroll
-    for (int i = 0; i < RI; ++i)
+    for (int u = 0; u < AI; ++u) {
+      const int e = tid + u * SU_THREADS, rr = e / NB, k = e - rr * NB;
+      As[rr][k] = anext[u];
+    }
+    float2 acc[RI];
 #pragma unroll
-      for (int j = 0; j < CJ; ++j) acc[i][j] = cfma(a[i], bk[j], acc[i][j]);
-  }
+    for (int i = 0; i < RI; ++i) acc[i] = old[i];
+    __syncthreads();
+    if (r0 + SU_RT < b) load(r0 + SU_RT);
 #pragma unroll
-  for (int i = 0; i < RI; ++i) {
-    const int r = r0 + ty + 16 * i;
-    if (r >= b) continue;
-    float2* Mr = M + (size_t)r * b + c0;
+    for (int i = 0; i < RI; ++i) {
+      const int rr = ty + 32 * i, r = r0 + rr;
 #pragma unroll
-    for (int j = 0; j < CJ; ++j)
-      if (upd[i] & (1u << j)) Mr[tx + 16 * j] = acc[i][j];
+      for (int k = 0; k < NB; ++k) acc[i] = cfma(As[rr][k], Bs[k][tx], acc[i]);
+      if (r < b && tx < nc) M[(size_t)r * b + cs + tx] = acc[i];
+    }
+    __syncthreads();
   }
 }
 
@@ -781,7 +768,6 @@ rr_status factor_wide_impl(rr_factors* fa) {
   float2* X = reinterpret_cast<float2*>(fa->X);
   const size_t bb = (size_t)b * b;
   const CUtensorMap* tA = reinterpret_cast<const CUtensorMap*>(fa->wmap[0]);
-  const CUtensorMap* tBin = reinterpret_cast<const CUtensorMap*>(fa->wmap[1]);
   const CUtensorMap* tBout = reinterpret_cast<const CUtensorMap*>(fa->wmap[2]);
   const int RB = 8;
   const size_t fsmem = (size_t)RB * b * sizeof(float2) + b * sizeof(int);
@@ -790,7 +776,7 @@ rr_status factor_wide_impl(rr_factors* fa) {
   const int nct_all = (b + GG_CT - 1) / GG_CT;
   const int pthreads = (b + 31) & ~31;  // one row per thread
   const size_t psmem = (size_t)b * GW_STAGE_LD * sizeof(float2);
-  RR_CUDA(cudaFuncSetAttribute(gjw_panel_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  RR_CUDA(cudaFuncSetAttribute(gjw_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)psmem));
   const int ncols = fa->factor_cols > 0 ? std::min(fa->factor_cols, nx) : nx;
   for (int i = 0; i < ncols; ++i) {
@@ -798,25 +784,47 @@ rr_status factor_wide_impl(rr_factors* fa) {
     gjw_rowpiv_init_kernel<<<(F * b + 255) / 256, 256, 0, st>>>(fa->rowpiv, F * b);
     rr_status s = launch_schur_f32(fa, i, st);
     if (s != RR_OK) return s;
-    // inner factorisation of one slab on stream sx: its panels and their
-    // rank-16 updates of the slab's other columns
-    auto inner = [&](int c0, cudaStream_t sx) -> rr_status {
+    // Inner factorisation of one slab: the panels in order on stream sx,
+    // each panel's update of the rest of the slab on stream sy.  Panel p+1
+    // applies panel p's transformation to its own columns itself, so it
+    // waits only for the slab update of panel p-1 (which reaches its
+    // columns) and runs beside the slab update of panel p (disjoint
+    // columns; the rows pivoted in p+1 change rowpiv from "none" to a
+    // column outside panel p, which that update reads as "not a pivot of p"
+    // either way).  The slab updates run in order on sy; sx joins sy at the
+    // end.
+    auto inner = [&](int c0, cudaStream_t sx, cudaStream_t sy) -> rr_status {
       const int c1 = std::min(b, c0 + GW_W);
-      for (int k0 = c0; k0 < c1; k0 += GW_NB) {
-        const int nbk = std::min(GW_NB, c1 - k0);
+      const int npan = (c1 - c0 + GW_NB - 1) / GW_NB;
+      cudaEvent_t* ev_pan = fa->ev_w;      // [4] ring: panel p done (on sx)
+      cudaEvent_t* ev_upd = fa->ev_w + 4;  // [4] ring: slab update of panel p done (on sy)
+      bool used = false;                   // sy took work (it joined sx's order by an event)
+      for (int p = 0; p < npan; ++p) {
+        const int k0 = c0 + p * GW_NB, nbk = std::min(GW_NB, c1 - k0);
+        if (p >= 2) RR_CUDA(cudaStreamWaitEvent(sx, ev_upd[(p - 2) & 3], 0));
         prof_begin(PROF_PANEL, sx);
-        gjw_panel_kernel<1><<<F, pthreads, psmem, sx>>>(b, k0, nbk, c0, c1, M, fa->rowpiv,
-                                                    fa->pivslot,
-                                                    reinterpret_cast<float2*>(fa->Bbuf), fa->flag);
+        gjw_panel_kernel<<<F, pthreads, psmem, sx>>>(b, k0, nbk, p > 0 ? k0 - GW_NB : -1, M,
+                                                     fa->rowpiv, fa->pivslot, fa->flag);
         prof_end(PROF_PANEL, sx);
-        // the rest of the slab (exact FP32 on the CUDA cores)
-        if (c1 - c0 > nbk) {
-          prof_begin(PROF_INNER, sx);
-          gjw_inner_update_kernel<<<dim3((b + IU_RT - 1) / IU_RT, F), IU_THREADS, 0, sx>>>(
-              b, k0, c0, c1, M, reinterpret_cast<const float2*>(fa->Bbuf), fa->rowpiv);
-          prof_end(PROF_INNER, sx);
+        RR_CUDA(cudaGetLastError());
+        // the slab's columns outside this panel and the next one
+        const int kn0 = p + 1 < npan ? k0 + GW_NB : -1;
+        const int ngroups = npan - 1 - (kn0 >= 0 ? 1 : 0);
+        if (ngroups > 0) {
+          RR_CUDA(cudaEventRecord(ev_pan[p & 3], sx));
+          RR_CUDA(cudaStreamWaitEvent(sy, ev_pan[p & 3], 0));
+          prof_begin(PROF_INNER, sy);
+          gjw_slab_update_kernel<<<dim3(ngroups, F), SU_THREADS, 0, sy>>>(
+              b, k0, nbk, kn0, c0, c1, M, fa->rowpiv, fa->pivslot);
+          prof_end(PROF_INNER, sy);
           RR_CUDA(cudaGetLastError());
+          RR_CUDA(cudaEventRecord(ev_upd[p & 3], sy));
+          used = true;
         }
+      }
+      if (used) {
+        RR_CUDA(cudaEventRecord(fa->ev_w[8], sy));
+        RR_CUDA(cudaStreamWaitEvent(sx, fa->ev_w[8], 0));
       }
       return RR_OK;
     };
@@ -829,7 +837,8 @@ rr_status factor_wide_impl(rr_factors* fa) {
     // stream's update reads as "not a pivot of this slab" either way).  The
     // next slab's pivot rows are gathered on the main stream after both.
     cudaStream_t st2 = fa->stream2;
-    if ((s = inner(0, st)) != RR_OK) return s;
+    cudaStream_t st3 = fa->stream3;
+    if ((s = inner(0, st, st3)) != RR_OK) return s;
     for (int c0 = 0; c0 < b; c0 += GW_W) {
       const int c1 = std::min(b, c0 + GW_W);
       if (c1 >= b && c0 == 0) break;  // one slab: no outer update
@@ -845,7 +854,7 @@ rr_status factor_wide_impl(rr_factors* fa) {
         if (st2 != nullptr) {
           RR_CUDA(cudaEventRecord(fa->ev_next, st));
           RR_CUDA(cudaStreamWaitEvent(st2, fa->ev_next, 0));
-          if ((s = inner(c1, st2)) != RR_OK) return s;
+          if ((s = inner(c1, st2, st3)) != RR_OK) return s;
           RR_CUDA(cudaEventRecord(fa->ev_panel, st2));
           if ((s = launch_gemm<SPLIT>(fa, tA, tBout, c0, GW_W, 0, s0, u1, nct_all, st)) != RR_OK)
             return s;
@@ -853,7 +862,7 @@ rr_status factor_wide_impl(rr_factors* fa) {
         } else {
           if ((s = launch_gemm<SPLIT>(fa, tA, tBout, c0, GW_W, 0, s0, u1, nct_all, st)) != RR_OK)
             return s;
-          if ((s = inner(c1, st)) != RR_OK) return s;
+          if ((s = inner(c1, st, st3)) != RR_OK) return s;
         }
       } else {
         if ((s = launch_gemm<SPLIT>(fa, tA, tBout, c0, GW_W, 0, s0, 0, 0, st)) != RR_OK) return s;

@@ -774,8 +774,12 @@ extern "C" rr_status rr_factor(rr_operator* op, int nshift, const double* shifts
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     cudaError_t e1 = cudaStreamCreateWithPriority(&fa->stream2, cudaStreamNonBlocking, hi_prio);
+    if (e1 == cudaSuccess)
+      e1 = cudaStreamCreateWithPriority(&fa->stream3, cudaStreamNonBlocking, hi_prio);
     if (e1 == cudaSuccess) e1 = cudaEventCreateWithFlags(&fa->ev_next, cudaEventDisableTiming);
     if (e1 == cudaSuccess) e1 = cudaEventCreateWithFlags(&fa->ev_panel, cudaEventDisableTiming);
+    for (int q = 0; q < 9 && e1 == cudaSuccess; ++q)
+      e1 = cudaEventCreateWithFlags(&fa->ev_w[q], cudaEventDisableTiming);
     if (e1 != cudaSuccess) return fail(cuda_status(e1, "rr_factor: stream/event creation"));
   }
   fa->shifts_h = new double2[nshift];
@@ -835,8 +839,14 @@ extern "C" rr_status rr_destroy_factors(rr_factors* fa) {
     cudaStreamSynchronize(fa->stream2);
     cudaStreamDestroy(fa->stream2);
   }
+  if (fa->stream3) {
+    cudaStreamSynchronize(fa->stream3);
+    cudaStreamDestroy(fa->stream3);
+  }
   if (fa->ev_next) cudaEventDestroy(fa->ev_next);
   if (fa->ev_panel) cudaEventDestroy(fa->ev_panel);
+  for (int q = 0; q < 9; ++q)
+    if (fa->ev_w[q]) cudaEventDestroy(fa->ev_w[q]);
   delete[] fa->shifts_h;
   delete fa;
   return RR_OK;

@@ -138,7 +138,9 @@ struct rr_factors {
   int prec;          // rr_precision
   cudaStream_t stream;
   cudaStream_t stream2;  // look-ahead panel stream (owned)
+  cudaStream_t stream3;  // slab-update stream of the wide factorisation (owned)
   cudaEvent_t ev_next, ev_panel;
+  cudaEvent_t ev_w[9];   // wide factorisation: panel / slab-update rings and the join
   size_t csz;        // bytes of one complex element of the factors
   void* G;           // [F][nx][b][b]   inverse of each Schur block
   void* X;           // [F][b][b] X_i = G_i C_i of the current column (transient)
