@@ -76,26 +76,46 @@ schur_kernel(OpView op, const double2* __restrict__ shifts, int i,
     }
     __syncthreads();
   }
+  // The CTA's rows (ny_blk points x q variables) share their stencil
+  // coefficients: stage them once, with the neighbour point of every y
+  // offset (-1: a Dirichlet ghost), so the per-entry loop reads shared
+  // memory only.
+  __shared__ T cA[SCHUR_Y * 4][12];  // coupling to column i-1 (slot dx = -1), term (dy, cp)
+  __shared__ T cD[SCHUR_Y * 4][12];  // diagonal block D_i (slot dx = 0)
+  __shared__ int jyt[SCHUR_Y][3];    // neighbour y of point y0 + ly at dy = -1, 0, 1
+  const int nt3 = 3 * q;
+  for (int e = threadIdx.x; e < ny_blk * q * nt3; e += blockDim.x) {
+    const int lr = e / nt3, t = e - lr * nt3;
+    const int ly = lr / q, comp = lr - ly * q;
+    const int iy = y0 + ly, dy = t / q - 1, cp = t - (t / q) * q;
+    const int jy = nbr_y(iy, dy, ny, op.periodic);
+    const size_t cf = ((size_t)i * b + iy * q + comp) * op.S;
+    cA[lr][t] = (jy >= 0 && Xp) ? coefv<T>(op, cf + slotx(-1, dy) * q + cp) : (T)0;
+    cD[lr][t] = jy >= 0 ? coefv<T>(op, cf + slotx(0, dy) * q + cp) : (T)0;
+  }
+  for (int e = threadIdx.x; e < ny_blk * 3; e += blockDim.x)
+    jyt[e / 3][e % 3] = nbr_y(y0 + e / 3, e % 3 - 1, ny, op.periodic);
+  __syncthreads();
   const int c = c0 + threadIdx.x;
   if (c >= b) return;
+  const int jc = c / q, cc = c - jc * q;  // column c = variable cc of point jc
   for (int ly = 0; ly < ny_blk; ++ly) {
     const int iy = y0 + ly;
     for (int comp = 0; comp < q; ++comp) {
-      const int r = iy * q + comp;
-      const size_t cf = ((size_t)i * b + r) * op.S;
+      const int r = iy * q + comp, lr = ly * q + comp;
       C val = (r == c) ? sh : czero<C>();
+      // D_i: the row's entries at column c (one per y offset landing on jc)
 #pragma unroll
-      for (int t = 0; t < 12; ++t) {  // 3 y neighbours x q <= 4 variables
-        if (t >= 3 * q) break;
-        const int dy = t / q - 1, cp = t - (t / q) * q;
-        const int jy = nbr_y(iy, dy, ny, op.periodic);
-        if (jy < 0) continue;
-        const T dv = coefv<T>(op, cf + slotx(0, dy) * q + cp);
-        if (jy * q + cp == c) val.x -= dv;
-        if (Xp) {
-          const T av = coefv<T>(op, cf + slotx(-1, dy) * q + cp);
+      for (int dy = 0; dy < 3; ++dy)
+        if (jyt[ly][dy] == jc) val.x -= cD[lr][dy * q + cc];
+      if (Xp) {
+#pragma unroll
+        for (int t = 0; t < 12; ++t) {  // 3 y neighbours x q <= 4 variables
+          if (t >= nt3) break;
+          const T av = cA[lr][t];
           // slot of point iy + dy: ly + 1 + dy (periodic wrap stays in the
           // staged range because the staged points are y0 - 1 .. y0 + ny_blk)
+          const int dy = t / q - 1, cp = t - (t / q) * q;
           if (av != (T)0) val = crfma(av, Xs[((ly + 1 + dy) * q + cp) * CB + threadIdx.x], val);
         }
       }
