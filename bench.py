@@ -39,7 +39,8 @@ BF16_PEAK_TFLOPS = 1900.0   # fallback burst figure
 # capture of the current kernels (profiles/), or None when the kernel changed
 # since the counters were taken.
 UPDATE_TRAFFIC = None
-SWEEP_TRAFFIC = None
+# sweep_tc2_kernel, one launch over all 64 frequencies (profiles/sweep_tc2_ns2d-8x256-k32_batch64.md)
+SWEEP_TRAFFIC = 310.0e6 + 18.3e6
 PRECISIONS = ("fp32", "fp32_bf16x3", "fp32_bf16x6")
 # tensor-core MMAs per FP32-level product of each operand split
 SPLIT_MMAS = {"fp32": ("tf32", 3), "fp32_bf16x3": ("bf16", 3), "fp32_bf16x6": ("bf16", 6)}
@@ -389,6 +390,9 @@ def run_ours(args):
                       "of the active frequencies, tcgen05)",
             "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
             "traffic": SWEEP_TRAFFIC, "peak_source": src,
+            "traffic_note": "ncu DRAM read + write of one launch over all F frequencies "
+                            "(the refinement's launches cover only the active ones)",
+            "algorithmic_full_launch": F * (b * b * 8 + 3 * b * k * 8),
             "algorithmic_per_launch": work / n_sw, "launches": n_sw,
             "avg_launch_us": tot_s / n_sw * 1e6,
             "algorithmic_note": "per block solve of one problem: (2 nx - 1) x (b^2 x 8 B of "
