@@ -797,15 +797,25 @@ rr_status gemm_step(rr_factors* fa, int k, int kp, int RT, int ob, int blk, cons
       const int nrt = (b + TC_RT - 1) / TC_RT;
       const int nch = (b + TC2_KC - 1) / TC2_KC;
       const int nsm = num_sms(d.device);
-      // split count: best balance of items over the persistent CTAs
+      // split count: the smallest whose items fill the persistent CTAs to
+      // 85 % (each split adds a partial block to write and combine), else
+      // the best balance.  The partial buffer holds 4 F b 64 complex, so up
+      // to 256 / k splits fit; few active problems (refinement corrections)
+      // take more splits to keep the SMs busy.
+      const int ks_max = std::min(16, std::max(1, 256 / k));
       int KS = 1;
       double best = 0.0;
-      for (int ksc = 1; ksc <= 4 && ksc <= nch; ++ksc) {
+      for (int ksc = 1; ksc <= ks_max && ksc <= nch; ++ksc) {
         const int cppc = (nch + ksc - 1) / ksc;
         const int ksr = (nch + cppc - 1) / cppc;
+        if (ksr > ks_max) continue;
         const long items = (long)nrt * Fa * ksr;
         const long waves = (items + nsm - 1) / nsm;
         const double eff = (double)items / (double)(waves * nsm);
+        if (eff >= 0.85) {
+          KS = ksr;
+          break;
+        }
         if (eff > best + 1e-9) { best = eff; KS = ksr; }
       }
       if (fa->tune_ks > 0) {  // tuned split count (at most the 4 partial buffers)
