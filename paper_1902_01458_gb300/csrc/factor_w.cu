@@ -343,7 +343,7 @@ __global__ void gjw_gather_kernel(int b, int c0, int c1, const float2* __restric
 // --------------------------------------------------------------- tensor GEMM
 // C[f][rows][cols] (+)= A[f] B[f] for complex FP32 data:
 //   A = M[f][:, ka .. ka + Kc)          (b x Kc, from M by TMA)
-//   B = Bbuf[f][0..Kc)[cols]            (Kc x b rows by TMA)
+//   B = Wbuf[f][0..Kc)[cols]            (Kc x b rows by TMA: the slab's pivot rows)
 // rows pivoted in [ka, ka + Kc) are overwritten with the product, the other
 // rows accumulate it, and the columns [ka, ka + Kc) are left alone.
 // Items (problem, 128-row tile, 64-column tile) over the column tiles of up
@@ -768,7 +768,7 @@ rr_status factor_wide_impl(rr_factors* fa) {
   float2* X = reinterpret_cast<float2*>(fa->X);
   const size_t bb = (size_t)b * b;
   const CUtensorMap* tA = reinterpret_cast<const CUtensorMap*>(fa->wmap[0]);
-  const CUtensorMap* tBout = reinterpret_cast<const CUtensorMap*>(fa->wmap[2]);
+  const CUtensorMap* tBout = reinterpret_cast<const CUtensorMap*>(fa->wmap[1]);
   const int RB = 8;
   const size_t fsmem = (size_t)RB * b * sizeof(float2) + b * sizeof(int);
   RR_CUDA(cudaFuncSetAttribute(gjw_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -521,9 +521,9 @@ static int encode_m_map(rr_factors* fa) {
 }
 
 // TMA maps of the wide factorisation (FP32 factors): chunks of 16 complex
-// columns x 128 rows of M (the left operand, read in place), and tiles of 16
-// rows x 64 complex of the gathered pivot rows Bbuf [F][32][b] (inner
-// update) and Wbuf [F][128][b] (outer update).
+// columns x 128 rows of M (the left operand of the rank-128 update, read in
+// place), and tiles of 16 rows x 64 complex of the gathered pivot rows Wbuf
+// [F][128][b] (its right operand).
 static int encode_wide_maps(rr_factors* fa) {
   const OpDev& d = fa->op->d;
   cudaDriverEntryPointQueryResult q;
@@ -539,8 +539,6 @@ static int encode_wide_maps(rr_factors* fa) {
   const cuuint64_t dm[3] = {(cuuint64_t)2 * d.b, (cuuint64_t)d.b, (cuuint64_t)fa->F};
   const cuuint64_t sm[2] = {(cuuint64_t)2 * d.b * 4, (cuuint64_t)2 * d.b * d.b * 4};
   const cuuint32_t boxA[3] = {32, 128, 1}, boxB[3] = {128, 16, 1};
-  const cuuint64_t di[3] = {(cuuint64_t)2 * d.b, 32, (cuuint64_t)fa->F};
-  const cuuint64_t si[2] = {(cuuint64_t)2 * d.b * 4, (cuuint64_t)2 * d.b * 32 * 4};
   const cuuint64_t dw[3] = {(cuuint64_t)2 * d.b, 128, (cuuint64_t)fa->F};
   const cuuint64_t sw[2] = {(cuuint64_t)2 * d.b * 4, (cuuint64_t)2 * d.b * 128 * 4};
   CUresult r0 = encode(reinterpret_cast<CUtensorMap*>(fa->wmap[0]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -548,14 +546,10 @@ static int encode_wide_maps(rr_factors* fa) {
                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   CUresult r1 = encode(reinterpret_cast<CUtensorMap*>(fa->wmap[1]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                       3, fa->Bbuf, di, si, boxB, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  CUresult r2 = encode(reinterpret_cast<CUtensorMap*>(fa->wmap[2]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                        3, fa->Wbuf, dw, sw, boxB, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return (r0 == CUDA_SUCCESS && r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) ? 1 : 0;
+  return (r0 == CUDA_SUCCESS && r1 == CUDA_SUCCESS) ? 1 : 0;
 }
 
 // ----------------------------------------------------------------- operator

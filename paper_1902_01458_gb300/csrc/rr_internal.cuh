@@ -158,7 +158,7 @@ struct rr_factors {
   int* rowpiv;       // [F][b] pivot column of each row (-1: not yet pivoted)
   int* pivslot;      // [F][b] pivot row of each column
   void* Wbuf;        // [F][128][b] gathered pivot rows of a slab (outer update)
-  alignas(64) unsigned char wmap[3][128];  // TMA maps: A chunks of M, Bbuf rows, Wbuf rows
+  alignas(64) unsigned char wmap[2][128];  // TMA maps: A chunks of M, Wbuf rows
   int* flag;         // [F] singular-pivot flags
   double2* shifts;   // [F] device
   double2* shifts_h; // [F] host copy
