@@ -1,6 +1,11 @@
 // Launch counting and optional CUDA-event timing of selected kernel classes.
 // Timing is off unless rr_profile_start enables classes; when on, an event
-// pair brackets every launch of an enabled class on its own stream.
+// pair brackets every launch of an enabled class on its own stream.  Safe to
+// call from several host threads (independent factors objects driven
+// concurrently): the counter is atomic, and an event pair is reserved under
+// a lock by the thread that begins it and closed by the same thread.
+#include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "rr_internal.cuh"
@@ -10,7 +15,9 @@ unsigned g_mask = 0;
 std::vector<cudaEvent_t> g_start[PROF_N], g_stop[PROF_N];
 size_t g_used[PROF_N] = {0};
 long long g_class_launches[PROF_N] = {0};
-long long g_launches = 0;
+std::atomic<long long> g_launches{0};
+std::mutex g_prof_mu;
+thread_local size_t t_open[PROF_N];  // event pair this thread opened, per class
 
 int g_suspended = 0;
 
@@ -48,8 +55,10 @@ void prof_count(int n) {
 void prof_begin(int cls, cudaStream_t st) {
   if (g_suspended) return;
   g_launches += 1;
-  g_class_launches[cls] += 1;
   if (!(g_mask & (1u << cls))) return;
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  g_class_launches[cls] += 1;
+  t_open[cls] = static_cast<size_t>(-1);  // no pair unless the events exist
   size_t i = g_used[cls];
   if (i >= g_start[cls].size()) {
     cudaEvent_t a, b;
@@ -59,17 +68,20 @@ void prof_begin(int cls, cudaStream_t st) {
     g_stop[cls].push_back(b);
   }
   cudaEventRecord(g_start[cls][i], st);
+  g_used[cls] = i + 1;  // reserved: this thread's prof_end closes pair i
+  t_open[cls] = i;
 }
 
 void prof_end(int cls, cudaStream_t st) {
   if (g_suspended || !(g_mask & (1u << cls))) return;
-  size_t i = g_used[cls];
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  const size_t i = t_open[cls];
   if (i >= g_stop[cls].size()) return;
   cudaEventRecord(g_stop[cls][i], st);
-  g_used[cls] = i + 1;
 }
 
 extern "C" rr_status rr_profile_start(unsigned mask) {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
   g_mask = mask;
   for (int c = 0; c < PROF_N; ++c) {
     g_used[c] = 0;
@@ -84,6 +96,7 @@ extern "C" rr_status rr_profile_read(int cls, double* ms, long long* launches) {
     set_error("rr_profile_read: unknown kernel class");
     return RR_ERR_ARG;
   }
+  std::lock_guard<std::mutex> lock(g_prof_mu);
   double total = 0.0;
   for (size_t i = 0; i < g_used[cls]; ++i) {
     cudaError_t e = cudaEventSynchronize(g_stop[cls][i]);
@@ -98,4 +111,4 @@ extern "C" rr_status rr_profile_read(int cls, double* ms, long long* launches) {
   return RR_OK;
 }
 
-extern "C" long long rr_launch_count(void) { return g_launches; }
+extern "C" long long rr_launch_count(void) { return g_launches.load(); }
