@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -73,6 +74,12 @@ def parse():
                    help="mixed: 512x256, k=32, 64 frequencies (default); "
                         "batched: the 128-problem uneven batch as one graph; "
                         "gradient: d(sum of leading gains)/d(base flow) at 256x128")
+    p.add_argument("--pipelines", type=int, default=1,
+                   help="mixed: the step's frequencies split into this many factors objects, "
+                        "each driven on its own stream by its own host thread, so one "
+                        "pipeline's FP64 phases overlap another's tensor-core phases (the "
+                        "per-class event times, and so the rooflines, then include the "
+                        "other pipelines' concurrent kernels)")
     p.add_argument("--fd-directions", type=int, default=64,
                    help="gradient: random directions checked by central differences")
     p.add_argument("--tune", type=int, default=1, help="batched: autotune the plan")
@@ -320,17 +327,61 @@ def run_ours(args):
     op = rr.Operator(g, flow, device=local)
     phi = op.phi()
 
-    def step(fa, s):
+    # The step's F frequencies run as P pipelines (interleaved subsets), each
+    # a factors object on its own stream driven by its own host thread: the
+    # library's calls block their thread only (refinement reads residual
+    # norms), so one pipeline's FP64 QR and residual phases overlap another's
+    # factorisation and sweeps.
+    P = max(1, min(args.pipelines, F))
+    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(P - 1)]
+
+    def parallel(fns):
+        if len(fns) == 1:
+            return [fns[0]()]
+        out, err = [None] * len(fns), []
+
+        def run(j):
+            try:
+                with torch.cuda.stream(streams[j]):
+                    out[j] = fns[j]()
+            except BaseException as e:  # noqa: BLE001 - re-raised below
+                err.append(e)
+        th = [threading.Thread(target=run, args=(j,)) for j in range(len(fns))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        if err:
+            raise err[0]
+        return out
+
+    def merge(infos):
+        m = dict(infos[0])
+        for i in infos[1:]:
+            for key in ("refine_iters", "refine_residual", "cqr_cond", "first_residual"):
+                m[key] = max(m[key], i[key])
+            m["refine_stagnated"] = m["refine_stagnated"] or i["refine_stagnated"]
+            m["problem_solves"] += i["problem_solves"]
+        return m
+
+    def step(fas, s):
         shifts, seeds, _ = batch_for(s, rank, world, F, wl.omegas, wl.seed0)
-        fa.refactor(shifts)
-        V, sh, i1 = fa.sketch(k, seeds, phi)
-        U, sig, i2 = fa.modes(V)
-        return sig, sh, i1, i2
+
+        def one(j):
+            def go():
+                fas[j].refactor(shifts[j::P])
+                V, sh, i1 = fas[j].sketch(k, seeds[j::P], phi)
+                U, sig, i2 = fas[j].modes(V)
+                return sig, sh, i1, i2
+            return go
+        res = parallel([one(j) for j in range(P)])
+        return ([r[0] for r in res], [r[1] for r in res], merge([r[2] for r in res]),
+                merge([r[3] for r in res]))
 
     # measured arithmetic peaks of this GPU (on-chip microbenchmarks)
     unit_peaks = {u: _lib.rr_measure_peak(u, local) for u in ("tf32", "bf16", "fp64", "fp32")}
     shifts0, _, _ = batch_for(0, rank, world, F, wl.omegas, wl.seed0)
-    fa = rr.Factors(op, shifts0, args.precision, stream)
+    fa = [rr.Factors(op, shifts0[j::P], args.precision, streams[j]) for j in range(P)]
     info_last = None
     for s in range(args.warmup):
         step(fa, s)
@@ -435,7 +486,8 @@ def run_ours(args):
     fp64 = None
     if not args.no_fp64 and rank == 0:
         F64 = args.fp64_batch
-        fa.close()
+        for f_ in fa:
+            f_.close()
         shifts, seeds, idx64 = batch_for(args.warmup, 0, 1, F64, wl.omegas, wl.seed0)
         ref32 = rr.Factors(op, shifts, args.precision, stream)
         V, sh32, ia = ref32.sketch(k, seeds, phi)
@@ -479,15 +531,19 @@ def run_ours(args):
                                      "step time, against the measured FP64 FMA peak"},
                 "note": "warmed: one untimed batch, then refactor + Algorithm 1 per step"}
     else:
-        fa.close()
+        for f_ in fa:
+            f_.close()
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers (the same pipelines:
+    # each thread builds its factors object, runs Algorithm 1 and copies its
+    # frequencies' U, V and sigma to pinned host buffers)
     e2e = None
     if not args.no_e2e:
         pin = lambda *shape, dt: torch.empty(*shape, dtype=dt, pin_memory=True)  # noqa: E731
-        Uh = pin(F, g.n, k, dt=torch.complex128)
-        Vh = pin(F, g.n, k, dt=torch.complex128)
-        Sh = pin(F, k, dt=torch.float64)
+        nf = [len(range(j, F, P)) for j in range(P)]
+        Uh = [pin(nf[j], g.n, k, dt=torch.complex128) for j in range(P)]
+        Vh = [pin(nf[j], g.n, k, dt=torch.complex128) for j in range(P)]
+        Sh = [pin(nf[j], k, dt=torch.float64) for j in range(P)]
         torch.cuda.synchronize(dev)
         barrier(pg, local)
         t0 = time.perf_counter()
@@ -497,17 +553,22 @@ def run_ours(args):
             op2 = rr.Operator(g, flow, device=local)
             h2d += 3 * g.npts * 8 + F * 16 + F * 8
             ph = op2.phi()
-            f2 = rr.Factors(op2, shifts, args.precision, stream)
-            V, sh, _ = f2.sketch(k, seeds, ph)
-            U, sig, _ = f2.modes(V)
-            Uh.copy_(U, non_blocking=True)
-            Vh.copy_(V, non_blocking=True)
-            Sh.copy_(sig, non_blocking=True)
-            torch.cuda.synchronize(dev)
-            d2h += Uh.numel() * 16 + Vh.numel() * 16 + Sh.numel() * 8
-            f2.close()
+
+            def one(j):
+                def go():
+                    f2 = rr.Factors(op2, shifts[j::P], args.precision, streams[j])
+                    V, sh, _ = f2.sketch(k, seeds[j::P], ph)
+                    U, sig, _ = f2.modes(V)
+                    Uh[j].copy_(U, non_blocking=True)
+                    Vh[j].copy_(V, non_blocking=True)
+                    Sh[j].copy_(sig, non_blocking=True)
+                    streams[j].synchronize()
+                    f2.close()
+                return go
+            parallel([one(j) for j in range(P)])
+            d2h += sum(Uh[j].numel() * 16 + Vh[j].numel() * 16 + Sh[j].numel() * 8
+                       for j in range(P))
             op2.close()
-            del U, V, sig, sh
         wall_e2e = time.perf_counter() - t0
         wall_e2e = max_over_ranks(pg, wall_e2e, dev)
         e2e = {"value": F * world * args.steps / wall_e2e, "unit": "frequencies/s",
@@ -530,7 +591,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": elapsed_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64+f64", "data": "synthetic",
-            "config": workload_config(g, k, world), "frequencies_per_step_per_gpu": F,
+            "config": workload_config(g, k, world),
+            "frequencies_per_step_per_gpu": F, "pipelines": P,
             "precision": f"mixed: fp32 factors, tensor-core updates and sweeps in the "
                          f"{args.precision} operand split, per-frequency fp64 refinement to "
                          f"1e-10 or the fp64 residual floor, fp64 CholeskyQR2 + Jacobi SVD",
