@@ -243,12 +243,19 @@ gjw_panel_kernel(int b, int k0, int nbk, int kp0, float2* __restrict__ Mall,
 // that panel's kernel updates itself:
 //   M[r, m] += M[r, K] B[:, m]      rows r not pivoted in K,
 //   M[r, m]  = M[r, K] B[:, m]      the pivot rows of K (T^{-1} B itself),
-// B[j][m] = M[pivslot[k0 + j], m] before this step.  CTA = (one 16-column
-// group of the slab, problem): it owns those columns of every row, so it
-// reads B for its columns before it writes any row (no other CTA writes
-// them).  Exact FP32 on the CUDA cores: a rank-16 contraction is bound by
-// moving the columns, not by its flops.
-constexpr int SU_THREADS = 512, SU_RT = 64;
+// B[j][m] = M[pivslot[k0 + j], m] before this step.  A cluster of SU_CL CTAs
+// owns one 16-column group of the slab for one problem, each CTA a range of
+// rows: every CTA reads B for the group's columns, then a cluster barrier,
+// then the CTAs write their rows (pivot rows included), so no B entry is
+// read after it was overwritten and no other cluster touches these columns.
+// Exact FP32 on the CUDA cores: a rank-16 contraction is bound by moving the
+// columns, not by its flops.
+constexpr int SU_THREADS = 256, SU_RT = 64, SU_CL = 4;
+
+__device__ __forceinline__ void su_cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
 
 __global__ void __launch_bounds__(SU_THREADS)
 gjw_slab_update_kernel(int b, int k0, int nbk, int kn0, int c0, int c1, float2* __restrict__ Mall,
@@ -257,51 +264,55 @@ gjw_slab_update_kernel(int b, int k0, int nbk, int kn0, int c0, int c1, float2* 
   __shared__ float2 Bs[NB][NB + 1];
   __shared__ float2 As[SU_RT][NB + 1];
   const int f = blockIdx.y;
-  // blockIdx.x-th 16-column group of [c0, c1) that is neither K nor the
-  // next panel
+  const int gsel = blockIdx.x / SU_CL, chunk = blockIdx.x % SU_CL;  // cluster = gsel
+  // gsel-th 16-column group of [c0, c1) that is neither K nor the next
+  // panel (the same for every CTA of the cluster)
   int cs = -1;
   for (int g = 0, cnt = 0; c0 + NB * g < c1; ++g) {
     const int c = c0 + NB * g;
     if (c == k0 || c == kn0) continue;
-    if (cnt++ == (int)blockIdx.x) {
+    if (cnt++ == gsel) {
       cs = c;
       break;
     }
   }
-  if (cs < 0) return;
+  if (cs < 0) return;  // the whole cluster returns
   const int nc = min(NB, c1 - cs);
+  const int rows_per = (b + SU_CL * SU_RT - 1) / (SU_CL * SU_RT) * SU_RT;
+  const int rbeg = chunk * rows_per, rend = min(b, rbeg + rows_per);
   float2* M = Mall + (size_t)f * b * b;
   const int* rowpiv = rowpiv_all + (size_t)f * b;
   const int* piv = pivslot_all + (size_t)f * b + k0;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // ty: 0 .. 31
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // ty: 0 .. 15
   for (int e = tid; e < NB * NB; e += SU_THREADS) {
     const int j = e / NB, c = e - j * NB;
     Bs[j][c] = (j < nbk && c < nc) ? M[(size_t)piv[j] * b + cs + c] : make_float2(0.f, 0.f);
   }
-  __syncthreads();  // every B entry read before any row (pivot rows included) is written
+  // every CTA of the cluster has read B before any of them writes a row
+  // (pivot rows included); the barrier also orders this CTA's Bs
+  su_cluster_sync();
   // Row tiles of SU_RT rows, software-pipelined: the old values and K's
   // entries of tile t + 1 are loaded into registers while tile t is computed.
-  constexpr int RI = SU_RT / 32, AI = SU_RT * NB / SU_THREADS;
+  constexpr int RI = SU_RT / 16, AI = SU_RT * NB / SU_THREADS;
   float2 old[RI], anext[AI];
-  bool pivn[RI];
   auto load = [&](int r0) {
 #pragma unroll
     for (int i = 0; i < RI; ++i) {
-      const int r = r0 + ty + 32 * i;
-      const bool live = r < b && tx < nc;
+      const int r = r0 + ty + 16 * i;
+      const bool live = r < rend && tx < nc;
       const int rp = live ? rowpiv[r] : -1;
-      pivn[i] = rp >= k0 && rp < k0 + NB;
-      old[i] = (live && !pivn[i]) ? M[(size_t)r * b + cs + tx] : make_float2(0.f, 0.f);
+      const bool pivot = rp >= k0 && rp < k0 + NB;
+      old[i] = (live && !pivot) ? M[(size_t)r * b + cs + tx] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < AI; ++u) {
       const int e = tid + u * SU_THREADS, rr = e / NB, k = e - rr * NB, r = r0 + rr;
-      anext[u] = (r < b && k < nbk) ? M[(size_t)r * b + k0 + k] : make_float2(0.f, 0.f);
+      anext[u] = (r < rend && k < nbk) ? M[(size_t)r * b + k0 + k] : make_float2(0.f, 0.f);
     }
   };
-  load(0);
+  if (rbeg < rend) load(rbeg);
 #pragma unroll 1
-  for (int r0 = 0; r0 < b; r0 += SU_RT) {
+  for (int r0 = rbeg; r0 < rend; r0 += SU_RT) {
 #pragma unroll
     for (int u = 0; u < AI; ++u) {
       const int e = tid + u * SU_THREADS, rr = e / NB, k = e - rr * NB;
@@ -311,16 +322,36 @@ gjw_slab_update_kernel(int b, int k0, int nbk, int kn0, int c0, int c1, float2* 
 #pragma unroll
     for (int i = 0; i < RI; ++i) acc[i] = old[i];
     __syncthreads();
-    if (r0 + SU_RT < b) load(r0 + SU_RT);
+    if (r0 + SU_RT < rend) load(r0 + SU_RT);
 #pragma unroll
     for (int i = 0; i < RI; ++i) {
-      const int rr = ty + 32 * i, r = r0 + rr;
+      const int rr = ty + 16 * i, r = r0 + rr;
 #pragma unroll
       for (int k = 0; k < NB; ++k) acc[i] = cfma(As[rr][k], Bs[k][tx], acc[i]);
-      if (r < b && tx < nc) M[(size_t)r * b + cs + tx] = acc[i];
+      if (r < rend && tx < nc) M[(size_t)r * b + cs + tx] = acc[i];
     }
     __syncthreads();
   }
+}
+
+// launch of the slab update: ngroups column groups x SU_CL-CTA clusters
+rr_status launch_slab_update(int b, int k0, int nbk, int kn0, int c0, int c1, int ngroups, int F,
+                             float2* M, const int* rowpiv, const int* pivslot, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ngroups * SU_CL, F, 1);
+  cfg.blockDim = dim3(SU_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = SU_CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  RR_CUDA(cudaLaunchKernelEx(&cfg, gjw_slab_update_kernel, b, k0, nbk, kn0, c0, c1, M, rowpiv,
+                             pivslot));
+  return RR_OK;
 }
 
 // Outer-update right operand: Bout[f][c][m] = M[P_{c0+c}][m] for m outside
@@ -814,10 +845,10 @@ rr_status factor_wide_impl(rr_factors* fa) {
           RR_CUDA(cudaEventRecord(ev_pan[p & 3], sx));
           RR_CUDA(cudaStreamWaitEvent(sy, ev_pan[p & 3], 0));
           prof_begin(PROF_INNER, sy);
-          gjw_slab_update_kernel<<<dim3(ngroups, F), SU_THREADS, 0, sy>>>(
-              b, k0, nbk, kn0, c0, c1, M, fa->rowpiv, fa->pivslot);
+          rr_status ls = launch_slab_update(b, k0, nbk, kn0, c0, c1, ngroups, F, M, fa->rowpiv,
+                                            fa->pivslot, sy);
           prof_end(PROF_INNER, sy);
-          RR_CUDA(cudaGetLastError());
+          if (ls != RR_OK) return ls;
           RR_CUDA(cudaEventRecord(ev_upd[p & 3], sy));
           used = true;
         }
