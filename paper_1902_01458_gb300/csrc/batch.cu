@@ -365,7 +365,7 @@ rr_status tune(rr_batch* B) {
   // K-split of each view's tensor-core sweep
   for (auto& G : B->groups)
     for (auto& v : G.views) {
-      if (!tc_prec(B->prec) || !v.fa->tma_ok || v.k % 2 != 0 || v.k > 32) continue;
+      if (!sweep_tc2_ok(v.fa, v.k)) continue;
       float best = INFINITY;
       int best_ks = 0;
       for (int ks = 0; ks <= 4; ++ks) {

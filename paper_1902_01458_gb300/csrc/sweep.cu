@@ -510,11 +510,12 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
                            ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
                            : 0;
   // x3 splits, per K step two MMAs: A_hi x [B_hi | B_lo] (N = 2 * 2k, both
-  // hi products in one pass over A_hi) and A_lo x B_hi.  Two accumulator sets
-  // (even and odd K steps) keep consecutive MMAs independent; the epilogue
-  // adds the six partial sums.  Set layout: [hi.hi | hi.lo | lo.hi], 3N
-  // columns.  BF16 x6, per K step three MMAs into one set of 6N columns:
-  // p0 x [q0 | q1 | q2], p1 x [q0 | q1], p2 x q0.
+  // hi products in one pass over A_hi) and A_lo x B_hi.  Up to 32 columns
+  // (3N <= 256) two accumulator sets (even and odd K steps) keep consecutive
+  // MMAs independent and the epilogue adds six partial sums; with 64 columns
+  // one set of 3N = 384 columns takes every K step.  Set layout: [hi.hi |
+  // hi.lo | lo.hi], 3N columns.  BF16 x6 (up to 32 columns), per K step three
+  // MMAs into one set of 6N columns: p0 x [q0 | q1 | q2], p1 x [q0 | q1], p2 x q0.
   const uint32_t ncols = X6 ? (6 * N <= 128 ? 128u : 6 * N <= 256 ? 256u : 512u)
                             : ((N <= 32) ? 256u : 512u);
   // work item t of this CTA -> (problem, row tile, contraction part)
@@ -537,6 +538,8 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
   const uint32_t set_cols = (uint32_t)(3 * N <= 128 ? 128 : 256);  // one accumulator set
+  const bool two_sets = !X6 && 3 * N <= 256;
+  const int nprod = (X6 || two_sets) ? 6 : 3;  // partial sums the epilogue adds
 
   // control thread: the stream of chunks of all this CTA's items.  With
   // stall set (a diagnostic of the bounded waits) the first CTA issues
@@ -653,8 +656,8 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
             mma(tmem + 3 * N, dA[q][1] + koff, dB[q] + koff, id2, acc);
             mma(tmem + 5 * N, dA[q][2] + koff, dB[q] + koff, id1, acc);
           } else {
-            const uint32_t set = tmem + (uint32_t)(kk & 1) * set_cols;
-            const uint32_t acc = (lc > 0 || kk > 1) ? 1u : 0u;
+            const uint32_t set = tmem + (two_sets ? (uint32_t)(kk & 1) * set_cols : 0u);
+            const uint32_t acc = (lc > 0 || kk > (two_sets ? 1 : 0)) ? 1u : 0u;
             mma(set, dA[q][0] + koff, dB[q] + koff, id2, acc);
             mma(set + 2 * N, dA[q][1] + koff, dB[q] + koff, id1, acc);
           }
@@ -683,10 +686,13 @@ sweep_tc2_kernel(const __grid_constant__ CUtensorMap tmap, int b, int k, int kp,
             tmem + ((uint32_t)(lq * 32 + 16 * sb) << 16) + (uint32_t)(hh * 32);
         tc::tmem_ld_16x256b_x4(ta, v);
 #pragma unroll
-        for (int a = 1; a < 6; ++a) {  // the six partial products
-          // x3: sets 0/1 x {hi.hi, hi.lo, lo.hi}; x6: p0.q0..2, p1.q0..1, p2.q0
-          const uint32_t col = X6 ? (uint32_t)(a * N)
-                                  : (uint32_t)(a / 3) * set_cols + (uint32_t)(a % 3) * N;
+        for (int a = 1; a < 6; ++a) {  // the partial products
+          // x3: sets 0/1 x {hi.hi, hi.lo, lo.hi} (one set: a < 3); x6:
+          // p0.q0..2, p1.q0..1, p2.q0
+          if (a >= nprod) break;
+          const uint32_t col = (X6 || !two_sets)
+                                   ? (uint32_t)(a * N)
+                                   : (uint32_t)(a / 3) * set_cols + (uint32_t)(a % 3) * N;
           tc::tmem_ld_16x256b_x4(ta + col, w);
 #pragma unroll
           for (int tt = 0; tt < 16; ++tt) v[tt] += w[tt];
@@ -770,10 +776,12 @@ rr_status launch_tc2(const CUtensorMap* tm, int grid_x, int b, int k, int kp, in
 }  // namespace
 
 // The split tensor-core sweep (sweep_tc2_kernel) serves FP32 factors with an
-// even block of at least 128 and an even k of at most 32 columns; only this
+// even block of at least 128 and an even k of at most 64 columns (32 for the
+// BF16 x6 split, whose six products need 6N accumulator columns); only this
 // path runs on a subset of the problems.
 bool sweep_tc2_ok(const rr_factors* fa, int k) {
-  return tc_prec(fa->prec) && k <= 32 && fa->tma_ok && (k % 2) == 0;
+  const int kmax = fa->prec == RR_FP32_BF16X6 ? 32 : 64;
+  return tc_prec(fa->prec) && k <= kmax && fa->tma_ok && (k % 2) == 0;
 }
 
 namespace {

@@ -255,7 +255,7 @@ def test_refinement_reports_non_convergence(env):
 
 
 @pytest.mark.parametrize("grid_shape", [(24, 20), (9, 40), (8, 50), (5, 88), (4, 128)])
-@pytest.mark.parametrize("k", [3, 16, 32])
+@pytest.mark.parametrize("k", [3, 16, 32, 48, 64])
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_tensor_core_sweeps_match_cuda_core_sweeps(env, grid_shape, k, adjoint):
     """One unrefined FP32 solve: the tensor-core path (tcgen05 3xTF32 trailing
