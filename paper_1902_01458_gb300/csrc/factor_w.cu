@@ -12,25 +12,26 @@
 // M = Q^T S^{-1} Q^T with (Q x)_j = x_{p_j}, so S^{-1}[j, p_m] = M[p_j, m].
 //
 // Levels, for every slab of W = 128 columns [c0, c1):
-//   inner, per panel K of 32 columns:
+//   inner, per panel K of 16 columns:
 //     panel  : one CTA per problem holds the tall panel M[:, K] in registers
-//              (one row per thread) and applies the 32 eliminations to it,
-//              recording the pivot rows P;
-//     update : the transformations of K applied to the rest of the slab,
-//              M[r, slab \ K] += M[r, K] * M_old[P, slab \ K] for rows r not in
-//              P and M[P, slab \ K] = M[P, K] * M_old[P, slab \ K] (the
-//              pivot rows take T^{-1} B itself: adding (T^{-1} - I) B to B
-//              would cancel when T^{-1} is small);
+//              (one row per thread), first applies the previous panel's
+//              transformation to it, then the 16 eliminations, recording the
+//              pivot rows P (gjw_panel_kernel);
+//     update : the transformations of K applied to the rest of the slab but
+//              the next panel, M[r, m] += M[r, K] * M_old[P, m] for rows r not
+//              in P and M[P, m] = M[P, K] * M_old[P, m] (the pivot rows take
+//              T^{-1} B itself: adding (T^{-1} - I) B to B would cancel when
+//              T^{-1} is small), in FP32 on the CUDA cores, beside the next
+//              panel on a third stream (gjw_slab_update_kernel);
 //   outer:
 //     gather : B = M[P_slab, outside the slab] (the pivot rows, saved before
 //              they change);
 //     update : the composed transformation of the slab's 128 eliminations
 //              applied at once, M[r, outside] += M[r, slab] * B (r not in
-//              P_slab), M[P_slab, outside] = M[P_slab, slab] * B.
-// Both updates are one tensor-core kernel (gjw_gemm_kernel): a complex GEMM
-// C += A B with A read from M (minus the identity at the pivot rows) and B
-// from the gathered rows, as a real GEMM on tcgen05 with the operands split
-// into TF32 or BF16 pieces (FP32-level products, FP32 accumulation in TMEM).
+//              P_slab), M[P_slab, outside] = M[P_slab, slab] * B, as a complex
+//              GEMM on tcgen05 with the operands split into TF32 or BF16
+//              pieces (FP32-level products, FP32 accumulation in TMEM;
+//              gjw_gemm_kernel).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -42,7 +43,7 @@
 namespace {
 
 constexpr int GW_W = 128;   // slab width (rank of the outer update)
-constexpr int GW_NB = 16;   // panel width (rank of the inner update)
+constexpr int GW_NB = 16;   // panel width (rank of the slab update)
 constexpr int GW_PANEL_MAX = 768;  // rows a panel CTA holds (two per thread)
 
 // ------------------------------------------------------------------- panel
@@ -666,8 +667,7 @@ gjw_gemm_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant
         if (row[u] >= b) continue;
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-          // the contraction's own columns (the panel, in the inner update)
-          // keep their values
+          // the contraction's own columns (the slab) keep their values
           const int c = cb + 4 * r;
           if (c < b && !(c >= g.ka && c < g.ka + g.Kc)) Mf[(size_t)row[u] * b + c] = cm[u][r];
         }
